@@ -1,0 +1,6 @@
+"""Plain FP64 CPU oracle of the FSLBM time step (arXiv 2207.13962).
+
+Test infrastructure only: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may use it; the product path never does.
+"""
+from .oracle import Oracle, build_oracle, lattice, feq, collide, select, reconstruct  # noqa: F401

@@ -1,0 +1,204 @@
+"""Whole-step pins of the oracle against what physics and the paper fix.
+
+* rest state: every variant keeps f = w_i, no conversion (Sec. 2.2);
+* hydrostatic flat interface stays at rest and keeps its cell types;
+* total liquid mass is conserved to round-off and the interface layer stays
+  closed under conversions in both directions (Eqs. nm-fslbm-mass-flux,
+  nm-fslbm-excess-mass);
+* standing gravity wave: period 2 pi / omega_0 with omega_0^2 = g k tanh(k d)
+  and viscous decay rate 2 nu k^2 (Sec. 4.1, analytical model);
+* Young-Laplace: a static cylinder carries the pressure jump sigma / R
+  (Eqs. nm-fslbm-pressure-gas, nm-fslbm-pressure-laplace, reading R7);
+* shear-wave decay pins nu = c_s^2 (tau - 1/2) (Eq. nm-lbm-viscosity);
+* body-force Poiseuille flow with half-way bounce-back is exact for TRT with
+  Lambda = 3/16 (pins Guo forcing and no-slip bounce-back);
+* bubble labels equal the connected components of the gas cells.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import curve_fit
+
+from oracle import Oracle, lattice
+from paper_2207_13962_gb300 import scenarios as S
+
+VARIANTS = ["NBRC", "NBKC", "OM", "OM3"]
+
+
+def _run(sc, **over):
+    o = Oracle(*sc.shape, **S.make_oracle_kwargs(sc, **over))
+    o.init(sc.fill, sc.flags, sc.velocity, sc.density)
+    return o
+
+
+def _closed(flags, shape, periodic, q):
+    """True when no liquid cell has a gas cell in its lattice neighbourhood."""
+    nx, ny, nz = shape
+    f = flags.reshape(nz, ny, nx)
+    gas = f == S.GAS
+    for dx, dy, dz in S.neighbour_offsets(q):
+        s = S._shift(S._shift(S._shift(gas, dz, 0, periodic[2], False), dy, 1, periodic[1], False),
+                     dx, 2, periodic[0], False)
+        if np.any(s & (f == S.LIQ)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_rest_state(variant):
+    sc = S.flat_interface(nx=6, ny=12, nz=3, depth=6.5, g=0.0, variant=variant)
+    o = _run(sc)
+    _, w, _ = lattice(19)
+    M0 = o.total_mass()
+    o.step(50)
+    r = o.read()
+    fluid = (r["flags"] == S.LIQ) | (r["flags"] == S.IFACE)
+    np.testing.assert_array_equal(r["flags"], sc.flags)
+    np.testing.assert_allclose(r["pdf"][:, fluid], np.repeat(w[:, None], fluid.sum(), 1), rtol=0, atol=1e-14)
+    assert abs(o.total_mass() - M0) / M0 < 1e-14
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_hydrostatic_flat_interface_stays_at_rest(variant):
+    sc = S.flat_interface(nx=6, ny=24, nz=3, depth=12.5, g=1e-5, variant=variant)
+    o = _run(sc)
+    M0 = o.total_mass()
+    o.step(400)
+    r = o.read()
+    _, u = o.moments()
+    fluid = (r["flags"] == S.LIQ) | (r["flags"] == S.IFACE)
+    np.testing.assert_array_equal(r["flags"], sc.flags)
+    # only the acoustic transient of the start-up (u = g/2 at t = 0) remains:
+    # velocities stay of the order of g and the surface does not move
+    assert np.abs(u[:, fluid]).max() < 5e-5
+    iface = r["flags"] == S.IFACE
+    assert np.abs(r["fill"][iface] - 0.5).max() < 1e-3
+    assert abs(o.total_mass() - M0) / M0 < 1e-13
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("q", [19, 27])
+def test_mass_conservation_and_closure(variant, q):
+    sc = S.random_interface(shape=(20, 18, 6), seed=3, q=q, variant=variant)
+    o = _run(sc)
+    M0 = o.total_mass()
+    to_l = to_g = 0
+    prev = sc.flags.copy()
+    for _ in range(120):
+        o.step(1)
+        fl = o.read()["flags"]
+        assert _closed(fl, sc.shape, sc.periodic, q)
+        to_l += int(np.sum((prev == S.IFACE) & (fl == S.LIQ)))
+        to_g += int(np.sum((prev == S.IFACE) & (fl == S.GAS)))
+        prev = fl
+    assert to_l > 0 and to_g > 0, "the stress case must convert in both directions"
+    assert abs(o.total_mass() - M0) / M0 < 1e-13
+
+
+def test_gravity_wave_dispersion_and_decay():
+    """L = 64, d = 32, a0 = 2, nu = 0.01; g chosen for a 1600-step period."""
+    L, d, a0, nu = 64, 32.0, 2.0, 0.01
+    k = 2 * np.pi / L
+    w0 = 2 * np.pi / 1600.0
+    g = w0 ** 2 / (k * np.tanh(k * d))
+    sc = S.gravity_wave(L=L, H=64, depth=d, amp_frac=a0 / L, g=g, nu=nu, variant="OM")
+    o = _run(sc)
+    M0 = o.total_mass()
+    a = []
+    for _ in range(3400):
+        a.append(o.read()["fill"].reshape(64, L)[:, 0].sum() - d)
+        o.step(1)
+    a = np.array(a)
+    t = np.arange(a.size)
+    model = lambda t, A, gam, w, p, c: A * np.exp(-gam * t) * np.cos(w * t + p) + c  # noqa: E731
+    p, _ = curve_fit(model, t, a, p0=[a0, 1e-4, w0, 0.0, 0.0])
+    period = 2 * np.pi / p[2]
+    assert abs(period / 1600.0 - 1.0) < 0.03, period
+    decay = p[1] / (2 * nu * k * k)
+    assert 0.85 < decay < 1.35, decay
+    assert abs(o.total_mass() - M0) / M0 < 1e-12
+
+
+@pytest.mark.parametrize("R", [12.0, 16.0])
+def test_laplace_pressure_static_cylinder(R):
+    sigma = 0.01
+    sc = S.static_drop(n=48, nz=1, R=R, sigma=sigma, nu=0.1)
+    o = _run(sc)
+    o.step(3000)
+    rho, _ = o.moments()
+    r = o.read()
+    X, Y = np.meshgrid(np.arange(48) + 0.5, np.arange(48) + 0.5)
+    inner = (np.sqrt((X - 24) ** 2 + (Y - 24) ** 2).reshape(-1) < R - 3) & (r["flags"] == S.LIQ)
+    dp = (rho[inner].mean() - 1.0) / 3.0
+    assert abs(dp / (sigma / R) - 1.0) < 0.06, dp
+
+
+def _all_liquid(shape, periodic, vel=None):
+    N = int(np.prod(shape))
+    return np.ones(N), np.full(N, S.LIQ, np.uint8), vel
+
+
+@pytest.mark.parametrize("collision", ["SRT", "TRT"])
+def test_shear_wave_decay(collision):
+    ny, U, nu = 32, 1e-3, 0.05
+    shape = (1, ny, 1)
+    y = np.arange(ny) + 0.5
+    vel = np.zeros(3 * ny)
+    vel[:ny] = U * np.sin(2 * np.pi * y / ny)
+    fill, flags, _ = _all_liquid(shape, (True, True, True))
+    o = Oracle(*shape, periodic=(True, True, True), collision=collision, omega=S.omega_from_nu(nu))
+    o.init(fill, flags, vel, None)
+    steps = 300
+    o.step(steps)
+    _, u = o.moments()
+    amp = 2.0 / ny * np.sum(u[0] * np.sin(2 * np.pi * y / ny))
+    k = 2 * np.pi / ny
+    expect = U * np.exp(-nu * k * k * steps)
+    # the initial f = f^eq state starts without the non-equilibrium shear part;
+    # the decay rate still has to match nu to well under one percent
+    assert abs(np.log(amp / U) / np.log(expect / U) - 1.0) < 0.01
+
+
+def test_poiseuille_trt_magic_exact():
+    H, nu, gx = 16, 0.1, 1e-6
+    shape = (1, H, 1)
+    fill, flags, _ = _all_liquid(shape, (True, False, True))
+    o = Oracle(*shape, periodic=(True, False, True), collision="TRT", trt_magic=3.0 / 16.0,
+               omega=S.omega_from_nu(nu), g=(gx, 0.0, 0.0))
+    o.init(fill, flags, None, None)
+    o.step(6000)
+    _, u = o.moments()
+    y = np.arange(H) + 0.5
+    ref = gx / (2 * nu) * y * (H - y)
+    np.testing.assert_allclose(u[0], ref, rtol=1e-6)
+
+
+def test_bubble_labels_are_connected_components():
+    from scipy import ndimage
+    sc = S.taylor_bubble(nx=24, ny=24, nz=60, D=20, bubble_d=12, bubble_len=16, z0=10, z_ref=30.0)
+    # add a second, separate bubble
+    fill = sc.fill.reshape(60, 24, 24).copy()
+    flags = sc.flags.reshape(60, 24, 24).copy()
+    flags[45:49, 10:14, 10:14] = S.GAS
+    fill[45:49, 10:14, 10:14] = 0.0
+    ring = np.zeros_like(flags, bool)
+    ring[44:50, 9:15, 9:15] = True
+    ring &= flags == S.LIQ
+    flags[ring] = S.IFACE
+    fill[ring] = 0.5
+    o = Oracle(24, 24, 60, periodic=(False, False, False), bubble_model=True)
+    o.init(fill.reshape(-1), flags.reshape(-1), None, None)
+    V, P, ids = o.bubbles()
+    lab, n = ndimage.label(flags == S.GAS, structure=ndimage.generate_binary_structure(3, 2))
+    assert len(V) == n == 2
+    lab = lab.reshape(-1)
+    gas = flags.reshape(-1) == S.GAS
+    # the label order follows the lowest cell index of each component
+    first = [np.flatnonzero(lab == k)[0] for k in range(1, n + 1)]
+    order = np.argsort(first)
+    for b, k in enumerate(order):
+        cells = lab == (k + 1)
+        assert np.all(ids[cells] == b)
+        iface = (flags.reshape(-1) == S.IFACE) & (ids == b)
+        expect = cells.sum() + np.sum(1.0 - fill.reshape(-1)[iface])
+        assert abs(V[b] - expect) < 1e-6
+    assert np.all(ids[~gas & (flags.reshape(-1) == S.LIQ)] == -1)

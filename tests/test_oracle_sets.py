@@ -1,0 +1,229 @@
+"""Pins of the boundary-condition variants (Sec. 3) in the oracle.
+
+* The worked example of Fig. 1 (golden fixture): the reconstructed PDFs of
+  NBRC, NBKC, OM and OM3 on the D2Q9 patch drawn in the paper.
+* Invariants of the sets over every gas pattern of D2Q9 and random patterns
+  of D3Q19 / D3Q27.
+* The force balance at the interface (Eq. fsbcv-force-balance-general) of the
+  reconstructed PDFs equals the closed forms printed for NBRC
+  (Eq. fsbcv-nbrc-force-balance), NBKC (Eq. fsbcv-nbkc-force-balance) and OM
+  (Eq. fsbcv-om-force-balance), derived in Appendix A.  These pin the
+  reconstruction formula (Eq. nm-fslbm-boundary-condition) term by term.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import feq, lattice, reconstruct, select
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+V = {"NBRC": 1, "NBKC": 2, "OM": 3, "OM3": 4}
+CS2 = 1.0 / 3.0
+
+
+def _index_of(c, vec):
+    for i in range(len(c)):
+        if c[i][0] == vec[0] and c[i][1] == vec[1] and c[i][2] == vec[2]:
+            return i
+    raise KeyError(vec)
+
+
+def test_fig1_worked_example():
+    with open(os.path.join(HERE, "golden", "fig1_reconstruction.json")) as fh:
+        fix = json.load(fh)
+    q = 9
+    c, _, _ = lattice(q)
+    gas = {tuple(p) for p in fix["cells"]["gas"]}
+    miss = np.zeros(q, np.int32)
+    for i in range(q):
+        src = (-c[i][0], -c[i][1])          # PDF i streams from x - c_i
+        if i != 0 and src in gas:
+            miss[i] = 1
+    a = fix["normal_arrow_drawn"]
+    drawn = np.array([a["to"][0] - a["from"][0], a["to"][1] - a["from"][1], 0.0])
+    n = -drawn / np.linalg.norm(drawn)     # n = grad(phi) points into the liquid
+    for name, expect in fix["reconstructed_velocities"].items():
+        R = select(q, V[name], V["NBKC"], n, miss)
+        got = {(int(c[i][0]), int(c[i][1])) for i in range(q) if R[i]}
+        assert got == {tuple(e) for e in expect}, name
+
+
+def _random_unit(rng):
+    v = rng.normal(size=3)
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_set_invariants(q):
+    rng = np.random.default_rng(10)
+    c, _, opp = lattice(q)
+    dims = 2 if q == 9 else 3
+    normals = []
+    for _ in range(12):
+        n = _random_unit(rng)
+        if dims == 2:
+            n[2] = 0.0
+            n /= np.linalg.norm(n)
+        normals.append(n)
+    normals += [np.array([1.0, 0, 0]), np.array([0, -1.0, 0]),
+                np.array([1.0, 1.0, 0]) / np.sqrt(2.0)]
+    if q == 9:
+        patterns = [np.array([(p >> (i - 1)) & 1 if i else 0 for i in range(q)], np.int32)
+                    for p in range(2 ** (q - 1))]
+    else:
+        patterns = [np.concatenate([[0], rng.integers(0, 2, q - 1)]).astype(np.int32)
+                    for _ in range(300)]
+    for n in normals:
+        dots = c.astype(np.float64) @ n
+        for miss in patterns:
+            R = {v: select(q, V[v], V["NBKC"], n, miss) for v in V}
+            R_fb_rc = select(q, V["OM3"], V["NBRC"], n, miss)
+            G = miss.astype(bool)
+            for v in V:
+                assert np.all(R[v][G]), "every missing PDF must be reconstructed"
+            np.testing.assert_array_equal(R["OM"], G)
+            assert R["NBRC"][0] and not R["NBKC"][0] and not R["OM"][0]
+            assert np.all(R["NBRC"] >= R["NBKC"])
+            # NBRC and NBKC differ only in ties n.c_i == 0
+            diff = R["NBRC"] & ~R["NBKC"]
+            assert np.all(dots[diff] == 0.0)
+            # generic normal: exactly one of i, ibar lies in the normal half-space
+            if np.all(dots[1:] != 0.0):
+                half = dots > 0
+                assert np.all(half[1:] ^ half[opp[1:]])
+            if G.sum() >= 3:
+                np.testing.assert_array_equal(R["OM3"], G)
+                np.testing.assert_array_equal(R_fb_rc, G)
+            else:
+                np.testing.assert_array_equal(R["OM3"], R["NBKC"])
+                np.testing.assert_array_equal(R_fb_rc, R["NBRC"])
+
+
+def _force(c, n, u, K, R, fstar, fin):
+    """Eq. fsbcv-force-balance-general: F_a / A."""
+    F = np.zeros(3)
+    for i in range(len(c)):
+        if K[i] or R[i]:
+            val = fstar[i] if K[i] else fin[i]
+            d = c[i] - u
+            F -= val * d * (n @ d)
+    return F
+
+
+def _setup(q, rng, generic=True):
+    c, w, opp = lattice(q)
+    c = c.astype(np.float64)
+    while True:
+        n = _random_unit(rng)
+        if q == 9:
+            n[2] = 0.0
+            n /= np.linalg.norm(n)
+        dots = c @ n
+        if not generic or np.all(np.abs(dots[1:]) > 1e-3):
+            break
+    u = np.zeros(3)
+    d = 2 if q == 9 else 3
+    u[:d] = rng.uniform(-0.08, 0.08, d)
+    fstar = w * rng.uniform(0.7, 1.3, len(w))
+    rho_g = rng.uniform(0.95, 1.05)
+    return c, w, opp, n, u, fstar, rho_g, dots
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_force_balance_nbrc(q):
+    rng = np.random.default_rng(20 + q)
+    for _ in range(40):
+        c, w, opp, n, u, fstar, rho_g, dots = _setup(q, rng)
+        # gas only on the normal side so that G- lies inside {n.c > 0}
+        miss = np.array([1 if (i and dots[i] > 0 and rng.random() < 0.5) else 0
+                         for i in range(q)], np.int32)
+        R = select(q, V["NBRC"], V["NBKC"], n, miss)
+        K = ~R
+        fin = reconstruct(q, R, rho_g, u, fstar, np.zeros(q))
+        lhs = _force(c, n, u, K, R, fstar, fin)
+        fe = feq(q, rho_g, u)
+        pg = rho_g * CS2
+        rhs = -n * pg + (n @ u) * (fstar[0] - fe[0]) * u
+        for i in range(q):
+            if dots[i] < 0:
+                rhs += 2 * (fstar[i] - fe[i]) * (c[i] * (n @ u) + u * (n @ c[i]))
+        np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_force_balance_nbkc(q):
+    rng = np.random.default_rng(30 + q)
+    for _ in range(40):
+        c, w, opp, n, u, fstar, rho_g, dots = _setup(q, rng)
+        miss = np.array([1 if (i and dots[i] > 0 and rng.random() < 0.5) else 0
+                         for i in range(q)], np.int32)
+        R = select(q, V["NBKC"], V["NBKC"], n, miss)
+        # the paper's K for NBKC is {n.c < 0}: the centre PDF is in neither sum
+        K = dots < 0
+        K[0] = False
+        fin = reconstruct(q, R, rho_g, u, fstar, np.zeros(q))
+        lhs = _force(c, n, u, K, R, fstar, fin)
+        fe = feq(q, rho_g, u)
+        pg = rho_g * CS2
+        rhs = -n * pg + (n @ u) * fe[0] * u
+        for i in range(q):
+            if dots[i] < 0:
+                rhs += 2 * (fstar[i] - fe[i]) * (c[i] * (n @ u) + u * (n @ c[i]))
+        np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
+def test_force_balance_om(q):
+    """OM closed form; the sum over T \\ G- u G+ is read as T \\ (G- u G+),
+    valid when no direction has gas on both sides (G- n G+ empty)."""
+    rng = np.random.default_rng(40 + q)
+    checked = 0
+    while checked < 40:
+        c, w, opp, n, u, fstar, rho_g, dots = _setup(q, rng, generic=False)
+        miss = np.concatenate([[0], rng.integers(0, 2, q - 1)]).astype(np.int32)
+        Gm = miss.astype(bool)
+        Gp = Gm[opp]
+        if np.any(Gm & Gp):
+            continue
+        checked += 1
+        R = select(q, V["OM"], V["NBKC"], n, miss)
+        K = ~R
+        fin = reconstruct(q, R, rho_g, u, fstar, np.zeros(q))
+        lhs = _force(c, n, u, K, R, fstar, fin)
+        fe = feq(q, rho_g, u)
+        pg = rho_g * CS2
+        rhs = -n * pg
+        for i in range(q):
+            d_m = c[i] - u
+            d_p = c[i] + u
+            if not Gm[i]:        # N-
+                rhs -= fstar[i] * d_m * (n @ d_m)
+            if Gp[i]:
+                rhs += fstar[i] * d_p * (n @ d_p)
+                rhs -= 2 * fe[i] * (c[i] * (n @ u) + u * (n @ c[i]))
+            if not Gm[i] and not Gp[i]:
+                rhs += fe[i] * d_m * (n @ d_m)
+        np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_force_balance_at_rest_normal_based(q):
+    """Steady interface cell (u = 0) with f* = f^eq(rho_g, 0): the normal-based
+    variants balance the gas pressure exactly (Sec. 3.1, 3.2)."""
+    rng = np.random.default_rng(50 + q)
+    c, w, opp = lattice(q)
+    c = c.astype(np.float64)
+    for _ in range(20):
+        n = _random_unit(rng)
+        rho_g = rng.uniform(0.95, 1.05)
+        fstar = feq(q, rho_g, np.zeros(3))
+        dots = c @ n
+        miss = np.array([1 if (i and dots[i] > 0) else 0 for i in range(q)], np.int32)
+        for v in ("NBRC", "NBKC"):
+            R = select(q, V[v], V["NBKC"], n, miss)
+            K = dots < 0
+            fin = reconstruct(q, R, rho_g, np.zeros(3), fstar, np.zeros(q))
+            F = _force(c, n, np.zeros(3), K, R, fstar, fin)
+            np.testing.assert_allclose(F, -n * rho_g * CS2, atol=1e-14)
