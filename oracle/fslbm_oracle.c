@@ -32,7 +32,11 @@
  *   R6  OM3 falls back to NBKC (selectable NBRC) when |G-| < 3.
  *   R7  gas density rho^G = 3 (p^V + sigma kappa), kappa = -div(n^) with n^
  *       pointing into the liquid (sum of principal curvatures).
- *   R8  the BC velocity is the cell's velocity of its previous collision.
+ *   R8  the density and velocity of a cell at time t are evaluated from its
+ *       post-collision PDFs: rho = sum f*_i, rho u = sum c_i f*_i - F/2 (equal
+ *       to the moments of its last collision, which conserves rho and adds F
+ *       to the momentum).  The BC uses this u(x,t); new interface cells
+ *       average these values over their neighbours at t+1.
  *   R9  force density F = rho g, not weighted by the fill level.
  *   R10 TRT: omega+ = omega, 1/omega- = 1/2 + Lambda/(1/omega+ - 1/2); Guo
  *       source split into symmetric (omega+) and antisymmetric (omega-) parts.
@@ -185,6 +189,28 @@ static void moments(const lattice* L, const double* f, const double* g,
   u[2] = jz / r + 0.5 * g[2];
 }
 
+/* Density and velocity of a cell from its post-collision PDFs (R8):
+ * rho = sum f*_i, u = (sum c_i f*_i)/rho - g/2. */
+static void post_moments(const lattice* L, const double* f, long stride,
+                         const double* g, double* rho, double* u) {
+  double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+  int i;
+  for (i = 0; i < L->q; ++i) r = r + f[i * stride];
+  for (i = 0; i < L->q; ++i) {
+    if (L->c[i][0] != 0) jx = jx + (double)L->c[i][0] * f[i * stride];
+  }
+  for (i = 0; i < L->q; ++i) {
+    if (L->c[i][1] != 0) jy = jy + (double)L->c[i][1] * f[i * stride];
+  }
+  for (i = 0; i < L->q; ++i) {
+    if (L->c[i][2] != 0) jz = jz + (double)L->c[i][2] * f[i * stride];
+  }
+  *rho = r;
+  u[0] = jx / r - 0.5 * g[0];
+  u[1] = jy / r - 0.5 * g[1];
+  u[2] = jz / r - 0.5 * g[2];
+}
+
 /* Collision (Eq. nm-lbm-collision with R1, R9, R10). */
 static void collide(const lattice* L, int collision, double omega,
                     double trt_magic, const double* g, const double* fin,
@@ -300,7 +326,8 @@ struct orc {
   double* f;    /* post-collision PDFs f*(t), direction-major [q][N] */
   double* fn;   /* next buffer */
   unsigned char* flag;
-  double *phi, *m, *rho, *u; /* u[3N] component-major */
+  double *phi, *m;
+  double* rho;               /* density of this step's collision (scratch) */
   int* bid;                  /* bubble id (gas/interface), -1 otherwise */
   int nb;                    /* number of bubbles */
   double *V0, *pV;           /* per bubble */
@@ -376,7 +403,6 @@ orc* orc_create(int nx, int ny, int nz, int per_x, int per_y, int per_z, int q,
   o->phi = (double*)calloc(N, sizeof(double));
   o->m = (double*)calloc(N, sizeof(double));
   o->rho = (double*)calloc(N, sizeof(double));
-  o->u = (double*)calloc(3 * N, sizeof(double));
   o->bid = (int*)calloc(N, sizeof(int));
   o->phis = (double*)calloc(N, sizeof(double));
   o->nhat = (double*)calloc(3 * N, sizeof(double));
@@ -391,7 +417,7 @@ orc* orc_create(int nx, int ny, int nz, int per_x, int per_y, int per_z, int q,
   o->phin = (double*)calloc(N, sizeof(double));
   o->mn = (double*)calloc(N, sizeof(double));
   o->share = (double*)calloc(N, sizeof(double));
-  if (!o->f || !o->fn || !o->flag || !o->phi || !o->m || !o->rho || !o->u ||
+  if (!o->f || !o->fn || !o->flag || !o->phi || !o->m || !o->rho ||
       !o->bid || !o->phis || !o->nhat || !o->kappa || !o->rhog || !o->cls ||
       !o->mark || !o->conv || !o->nflag || !o->isnew || !o->dfr || !o->phin || !o->mn ||
       !o->share) {
@@ -409,7 +435,6 @@ void orc_destroy(orc* o) {
   free(o->phi);
   free(o->m);
   free(o->rho);
-  free(o->u);
   free(o->bid);
   free(o->V0);
   free(o->pV);
@@ -476,15 +501,10 @@ int orc_init(orc* o, const double* fill, const unsigned char* flags,
     int fl = o->flag[c];
     o->phi[c] = (fl == LIQ) ? 1.0 : (fl == IFACE) ? fill[c] : 0.0;
     o->m[c] = (fl == LIQ) ? r : (fl == IFACE) ? fill[c] * r : 0.0;
+    o->rho[c] = 0.0;
     if (fl == LIQ || fl == IFACE) {
-      o->rho[c] = r;
-      o->u[c] = ux;
-      o->u[N + c] = uy;
-      o->u[2 * N + c] = uz;
       for (i = 0; i < L->q; ++i) o->f[i * N + c] = feq_i(L, i, r, ux, uy, uz);
     } else {
-      o->rho[c] = 0.0;
-      o->u[c] = o->u[N + c] = o->u[2 * N + c] = 0.0;
       for (i = 0; i < L->q; ++i) o->f[i * N + c] = 0.0;
     }
   }
@@ -700,7 +720,8 @@ static void stream_collide(orc* o) {
     if (fl == IFACE) {
       double dm = 0.0;
       double nh[3] = {o->nhat[c], o->nhat[N + c], o->nhat[2 * N + c]};
-      double uc[3] = {o->u[c], o->u[N + c], o->u[2 * N + c]};
+      double rc, uc[3];
+      post_moments(L, o->f + c, N, o->g, &rc, uc);
       select_R(L, o->variant, o->om3_fallback, nh, miss, recon);
       reconstruct(L, recon, o->rhog[c], uc, fx, fin);
       /* mass exchange (Eq. nm-fslbm-mass-flux, R11, R12) */
@@ -723,9 +744,6 @@ static void stream_collide(orc* o) {
     collide(L, o->collision, o->omega, o->trt_magic, o->g, fin, fout, &rho, u);
     for (i = 0; i < q; ++i) o->fn[i * N + c] = fout[i];
     o->rho[c] = rho;
-    o->u[c] = u[0];
-    o->u[N + c] = u[1];
-    o->u[2 * N + c] = u[2];
     if (fl == IFACE) o->phin[c] = o->mn[c] / rho;
   }
 }
@@ -811,10 +829,12 @@ static void convert(orc* o) {
         long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
         if (n < 0) continue;
         if (o->nflag[n] == LIQ || (o->nflag[n] == IFACE && !o->isnew[n])) {
-          sr = sr + o->rho[n];
-          sx = sx + o->u[n];
-          sy = sy + o->u[N + n];
-          sz = sz + o->u[2 * N + n];
+          double rn, un[3];
+          post_moments(L, o->fn + n, N, o->g, &rn, un);
+          sr = sr + rn;
+          sx = sx + un[0];
+          sy = sy + un[1];
+          sz = sz + un[2];
           ++cnt;
         }
       }
@@ -829,14 +849,14 @@ static void convert(orc* o) {
       }
       for (i = 0; i < q; ++i) o->fn[i * N + c] = feq_i(L, i, rb, ub[0], ub[1], ub[2]);
       o->rho[c] = rb;
-      o->u[c] = ub[0];
-      o->u[N + c] = ub[1];
-      o->u[2 * N + c] = ub[2];
       o->m[c] = 0.0;
       o->phi[c] = 0.0;
     } else if (o->isnew[c] == 2) {
       int best = -1;
-      o->m[c] = o->rho[c];
+      double rn, un[3];
+      post_moments(L, o->fn + c, N, o->g, &rn, un);
+      o->rho[c] = rn;
+      o->m[c] = rn;
       o->phi[c] = 1.0;
       coords(o, c, &x, &y, &z);
       for (i = 1; i < q; ++i) {
@@ -920,8 +940,18 @@ void orc_read(const orc* o, double* pdf, double* fill, unsigned char* flags,
 }
 
 void orc_read_moments(const orc* o, double* rho, double* u) {
-  if (rho) memcpy(rho, o->rho, sizeof(double) * (size_t)o->N);
-  if (u) memcpy(u, o->u, sizeof(double) * 3 * (size_t)o->N);
+  long c, N = o->N;
+  for (c = 0; c < N; ++c) {
+    double r = 0.0, v[3] = {0.0, 0.0, 0.0};
+    if (o->flag[c] == LIQ || o->flag[c] == IFACE)
+      post_moments(&o->L, o->f + c, N, o->g, &r, v);
+    if (rho) rho[c] = r;
+    if (u) {
+      u[c] = v[0];
+      u[N + c] = v[1];
+      u[2 * N + c] = v[2];
+    }
+  }
 }
 
 int orc_bubbles(const orc* o, double* volume, double* pressure, int* ids_cell,

@@ -43,7 +43,8 @@ long orc_steps_done(const orc* o);
 /* Any pointer may be NULL.  pdf[q*N] direction-major post-collision PDFs. */
 void orc_read(const orc* o, double* pdf, double* fill, unsigned char* flags,
               double* mass);
-/* rho[N], u[3N] of the last collision (valid on liquid/interface cells). */
+/* rho[N], u[3N] of each liquid/interface cell evaluated from its current
+ * post-collision PDFs (rho = sum f*, rho u = sum c f* - F/2); 0 elsewhere. */
 void orc_read_moments(const orc* o, double* rho, double* u);
 /* Geometry of the current state (before the next step): nhat[3N], kappa[N]
  * (kappa only meaningful on interface cells), phis[N] smoothed fill. */
