@@ -1,0 +1,425 @@
+"""Benchmark of the FSLBM time step on GB300.
+
+Default workload: the rising Taylor bubble, 160 x 160 x 1024 cells, D3Q19
+TRT, FP32 PDFs (fill level and mass in FP64), free-surface BC variant OM,
+curvature-driven Laplace pressure and per-bubble volume tracking: one step
+runs every stage of the method (geometry, bulk stream-collide, interface BC
+and mass exchange, conversion, excess mass, bubble pressure).
+
+Prints ONE JSON line (rank 0).  ``value`` is whole-job MLUPS (cell updates
+per second over all cells of all ranks); the timed region holds exactly
+``--steps`` steps with the state resident in HBM.  ``e2e`` repeats the
+measurement through the C ABI with host buffers: initial state uploaded from
+pinned host memory and the fill-level field read back inside the timed region.
+
+``--impl reference`` times the plain CPU oracle (single thread, as it stands)
+on a bounded sample of the same workload; it is the only other use of
+``oracle/`` here besides the ``cpu_baseline`` field.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FSLBM MLUPS and % HBM roofline on 1 GB300; batched/served vs plain at stated error; p50/p99"
+Q = 19
+S_BYTES = {"FP32": 4, "FP64": 8, "FP16S": 2, "BF16S": 2}
+DTYPE = {"FP32": "f32", "FP64": "f64", "FP16S": "f32 (fp16 storage)", "BF16S": "f32 (bf16 storage)"}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- workloads
+
+def make_workload(name: str, variant: str):
+    from paper_2207_13962_gb300 import scenarios as S
+    if name == "taylor_bubble":
+        sc = S.taylor_bubble(variant=variant)
+        desc = ("rising Taylor bubble 160x160x1024, tube D=128, bubble 96x256, D3Q19 TRT, "
+                "g=1e-6, sigma=1e-4, nu=5e-3, bubble model")
+    elif name == "dam_break":
+        sc = S.dam_break(variant=variant)
+        desc = "rectangular dam break 256x128x64, column 64^3, D3Q19 TRT, g=1e-5, nu=1e-3, no-slip"
+    elif name == "box512":
+        sc = S.flat_interface(nx=512, ny=512, nz=512, depth=505.5, g=1e-5, variant=variant)
+        desc = "512^3 liquid box with a flat surface (bulk ceiling), D3Q19 TRT"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return sc, desc
+
+
+def oracle_sample(sc, name: str, zlo: int, zhi: int):
+    """A z-slab of the workload's initial state (walls at the cut faces)."""
+    from paper_2207_13962_gb300 import scenarios as S
+    nx, ny, nz = sc.shape
+    zlo, zhi = max(0, zlo), min(nz, zhi)
+    sl = slice(zlo * nx * ny, zhi * nx * ny)
+    fill = sc.fill[sl].copy()
+    flags = sc.flags[sl].copy()
+    den = None if sc.density is None else sc.density[sl].copy()
+    vel = None
+    if sc.velocity is not None:
+        N = nx * ny * nz
+        vel = np.concatenate([sc.velocity[a * N:(a + 1) * N][sl] for a in range(3)])
+    shape = (nx, ny, zhi - zlo)
+    per = (sc.periodic[0], sc.periodic[1], False)
+    # the cut faces become walls: restore closure in case a cut exposed a liquid-gas contact
+    f3 = flags.reshape(shape[2], ny, nx)
+    p3 = fill.reshape(shape[2], ny, nx)
+    gas = f3 == S.GAS
+    for dx, dy, dz in S.neighbour_offsets(sc.q):
+        sh = S._shift(S._shift(S._shift(gas, dz, 0, per[2], False), dy, 1, per[1], False), dx, 2, per[0], False)
+        fix = sh & (f3 == S.LIQ)
+        f3[fix] = S.IFACE
+        p3[fix] = 1.0
+    return S.Scenario(f"{name}[z={zlo}:{zhi}]", shape, per, fill, flags, vel, den, q=sc.q,
+                      collision=sc.collision, variant=sc.variant, omega=sc.omega, g=sc.g,
+                      sigma=sc.sigma, bubble_model=sc.bubble_model)
+
+
+def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50):
+    """Oracle MLUPS on a bounded sample of the workload (single host thread)."""
+    from oracle import Oracle
+    from paper_2207_13962_gb300 import scenarios as S
+    if name == "taylor_bubble":
+        smp = oracle_sample(sc, name, 352, 416)
+    elif name == "box512":
+        smp = oracle_sample(sc, name, 448, 512)
+    else:
+        smp = sc
+    o = Oracle(*smp.shape, **S.make_oracle_kwargs(smp))
+    o.init(smp.fill, smp.flags, smp.velocity, smp.density)
+    o.step(1)
+    done, t0 = 0, time.perf_counter()
+    while done < max_steps:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > steps_budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": smp.N * done / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{smp.name}: {smp.shape[0]}x{smp.shape[1]}x{smp.shape[2]} cells of the same "
+                      f"initial state, {done} steps after 1 warm-up step, FP64, 1 host thread",
+            "seconds": dt}
+
+
+# -------------------------------------------------------------- our arm
+
+def bench_ours(args, ws, rank, local):
+    import torch
+    from paper_2207_13962_gb300 import fslbm
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = args.precision
+    sc, desc = make_workload(args.workload, args.variant)
+    stream = torch.cuda.Stream()
+    ctx = fslbm.context_for(sc, precision=prec, stream=stream.cuda_stream)
+    N = sc.N
+
+    # warm-up
+    ctx.step(args.warmup)
+    if ctx.sync() != 0:
+        raise SystemExit(f"unstable during warm-up: {ctx.lib.fslbm_last_error(ctx.h).decode()}")
+    obs0 = ctx.observables()
+    segs_bytes = None
+
+    # ---- timed region: exactly K steps, state resident in HBM
+    ctx.set_timing(False)  # resets the launch counter; CUDA-graph launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ck = clocks.stop()
+    ms_local = e0.elapsed_time(e1)
+    _, launches = ctx.stage_times()
+    st = ctx.sync()
+    obs1 = ctx.observables()
+    ms = max_over_ranks(ms_local, ws)
+    value = N * ws * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- per-stage CUDA-event timing (kernels launched one by one on the
+    # context's stream) for the roofline of the dominant kernel
+    ctx.set_timing(True)
+    ctx.step(args.steps)
+    times, _ = ctx.stage_times()
+    ctx.set_timing(False)
+    obs2 = ctx.observables()
+    bulk_ms = times["bulk"] / args.steps
+    n_liq = 0.5 * (obs1["n_liquid"] + obs2["n_liquid"])
+    nseg = ctx.work_counts()["liquid_segments"]
+    # algorithmic bytes of one bulk launch: read + write q PDFs per liquid
+    # cell, one flag byte per cell of the swept 32-cell segments
+    alg_bytes = n_liq * 2 * Q * S_BYTES[prec] + nseg * 32
+    achieved = alg_bytes / (bulk_ms * 1e-3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    share = {k: round(v / max(sum(times.values()), 1e-12), 4) for k, v in times.items()}
+
+    # ---- end to end through the C ABI with host buffers
+    pin_fill = torch.from_numpy(sc.fill).pin_memory()
+    pin_flags = torch.from_numpy(sc.flags).pin_memory()
+    pin_den = torch.from_numpy(sc.density).pin_memory() if sc.density is not None else None
+    out_fill = torch.empty(N, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    rc = ctx.init_raw(pin_fill.data_ptr(), pin_flags.data_ptr(), None,
+                      pin_den.data_ptr() if pin_den is not None else None)
+    if rc != 0:
+        raise SystemExit("e2e init failed")
+    ctx.step(args.steps)
+    rc = ctx.lib.fslbm_read_fields(ctx.h, None, fslbm.C.c_void_p(out_fill.data_ptr()), None, None)
+    if rc != 0:
+        raise SystemExit("e2e read failed")
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    h2d = sc.fill.nbytes + sc.flags.nbytes + (sc.density.nbytes if sc.density is not None else 0)
+    d2h = out_fill.numel() * 8
+    e2e = {"value": N * ws * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "note": f"fslbm_init from pinned host arrays + {args.steps} steps + fill-level readback"}
+
+    # ---- secondary workload: the rectangular dam break (configs' second entry)
+    other = {}
+    if args.workload == "taylor_bubble" and not args.no_secondary:
+        sc2, desc2 = make_workload("dam_break", args.variant)
+        c2 = fslbm.context_for(sc2, precision=prec, stream=stream.cuda_stream)
+        c2.step(args.warmup)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        c2.step(args.steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        dms = f0.elapsed_time(f1) / args.steps
+        o2 = c2.observables()
+        other["dam_break_256x128x64"] = {
+            "mlups": round(sc2.N / dms / 1e3, 1), "ms_per_step": round(dms, 5),
+            "mflups": round((o2["n_liquid"] + o2["n_interface"]) / dms / 1e3, 1),
+            "note": "L2 not flushed: the touched state (~40 MB) fits in L2"}
+        c2.close()
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = run_oracle_sample(sc, args.workload)
+            cpu.pop("seconds", None)
+        line = {
+            "metric": METRIC,
+            "value": round(value, 2),
+            "unit": "MLUPS",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 6),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": DTYPE[prec],
+            "data": "synthetic (seeded generator, no dataset)",
+            "config": {
+                "workload": desc,
+                "cells_per_gpu": N,
+                "lattice": "D3Q19", "collision": "TRT", "precision": prec, "bc_variant": args.variant,
+                "parallelism": f"{ws} independent replica(s), one domain per GPU, no collective",
+                "l2": f"inputs larger than L2: {2 * Q * S_BYTES[prec] * N / 1e9:.2f} GB of PDFs",
+                "mflups": round((obs1["n_liquid"] + obs1["n_interface"]) * ws * args.steps / (ms * 1e-3) / 1e6, 2),
+                "interface_cells": obs1["n_interface"],
+                "mass_drift_rel": (obs1["total_mass"] - obs0["total_mass"]) / obs0["total_mass"],
+                "status": int(st),
+            },
+            "roofline": {
+                "bound": "hbm", "kernel": "k_bulk (pull stream-collide of liquid cells)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
+                "traffic": None,
+                "alg_bytes_per_launch": int(alg_bytes), "launch_ms": round(bulk_ms, 6),
+                "stage_share": share,
+            },
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": ck,
+            "other_workloads": other,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line
+
+
+# --------------------------------------------------------- reference arm
+
+def bench_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    from oracle.oracle import build_oracle
+    build_oracle()
+    sc, desc = make_workload(args.workload, args.variant)
+    vals = []
+    for _ in range(args.warmup):
+        run_oracle_sample(sc, args.workload, steps_budget_s=3.0, max_steps=2)
+    samp = None
+    t_total = 0.0
+    for _ in range(args.steps):
+        r = run_oracle_sample(sc, args.workload, steps_budget_s=6.0, max_steps=10)
+        vals.append(r["value"])
+        samp = r["sample"]
+        t_total += r["seconds"]
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000.0 * t_total / max(args.steps, 1), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator, no dataset)",
+        "config": {"workload": desc, "sample": samp},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": samp},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "dam_break", "box512"])
+    ap.add_argument("--precision", default="FP32", choices=list(S_BYTES))
+    ap.add_argument("--variant", default="OM", choices=["NBRC", "NBKC", "OM", "OM3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        bench_reference(args, ws, rank)
+        return
+    bench_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * fslbm.h - C ABI of the GB300 (sm_103a) free-surface lattice Boltzmann step.
+ *
+ * The library advances the free-surface lattice Boltzmann method (FSLBM) of
+ * Schwarzmeier & Ruede, arXiv 2207.13962, Sec. 2 (LBM with SRT/TRT collision
+ * and Guo forcing, Eqs. nm-lbm-*; free-surface extension, Eqs. nm-fslbm-*)
+ * with the free-surface boundary condition in the four variants of Sec. 3
+ * (NBRC Eq. fsbcv-nbrc, NBKC Eq. fsbcv-nbkc, OM Eq. fsbcv-om-sets, OM3
+ * Eq. fsbcv-om3).  Every step of the path runs in hand-written CUDA kernels.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ *  * Cells are indexed c = x + nx * (y + ny * z).
+ *  * Cell types (flags): 0 gas, 1 interface, 2 liquid, 3 obstacle (Sec. 2.2).
+ *    Cells outside a non-periodic domain face are no-slip walls.
+ *  * PDFs are ordered i = 0 rest, 1..6 faces (+x,-x,+y,-y,+z,-z), 7..18 edges,
+ *    19..26 corners (D3Q27 only); directions 2k-1 and 2k are opposite.
+ *    Full table: (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1)
+ *    (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+ *    (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1) (1,1,1) (-1,-1,-1) (1,1,-1)
+ *    (-1,-1,1) (1,-1,1) (-1,1,-1) (-1,1,1) (1,-1,-1).
+ *  * Host arrays passed in are owned by the caller and copied; the context
+ *    owns all device memory it allocates.  Nothing is retained after a call.
+ *  * Every call returns a status.  A call that fails with FSLBM_EINVAL leaves
+ *    the context untouched; the message of the last failure is returned by
+ *    fslbm_last_error().
+ *  * Work is enqueued on params.stream (a cudaStream_t, NULL = the legacy
+ *    default stream).  fslbm_step is asynchronous; fslbm_observables,
+ *    fslbm_read_fields and fslbm_sync synchronize that stream.
+ */
+#ifndef FSLBM_H
+#define FSLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fslbm_ctx fslbm_ctx;
+
+typedef enum {
+  FSLBM_OK = 0,
+  FSLBM_EINVAL = 1,     /* bad argument or initial state; nothing changed   */
+  FSLBM_ENOMEM = 2,     /* device or host allocation failed                  */
+  FSLBM_ECUDA = 3,      /* a CUDA call failed; see fslbm_last_error()        */
+  FSLBM_EUNSTABLE = 4,  /* |u|^2 >= c_s^2, rho <= 0 or a NaN was seen
+                           (the instability of Sec. 4.2); fields stay readable */
+  FSLBM_ETIMEOUT = 5,   /* a bounded device wait gave up                     */
+  FSLBM_ESTATE = 6,     /* call out of order (e.g. step before init)         */
+  FSLBM_ECAPACITY = 7   /* the interface band outgrew its preallocated list  */
+} fslbm_status;
+
+/* Velocity sets D3Q19 and D3Q27 (Sec. 2.1). */
+typedef enum { FSLBM_D3Q19 = 19, FSLBM_D3Q27 = 27 } fslbm_lattice;
+
+/* Collision: SRT, Eq. nm-lbm-collision-operator (relaxing towards f^eq);
+ * TRT: two relaxation rates with the magic parameter trt_magic. */
+typedef enum { FSLBM_SRT = 0, FSLBM_TRT = 1 } fslbm_collision;
+
+/* Free-surface boundary-condition variants (i)-(iv) of Sec. 3. */
+typedef enum {
+  FSLBM_NBRC = 1, /* Eq. fsbcv-nbrc: R = {n.c_i >= 0} (centre included)   */
+  FSLBM_NBKC = 2, /* Eq. fsbcv-nbkc: R = {n.c_i > 0} (centre kept)        */
+  FSLBM_OM = 3,   /* Eq. fsbcv-om-sets: R = G- (only missing PDFs)        */
+  FSLBM_OM3 = 4   /* Eq. fsbcv-om3: OM if |G-| >= 3, else the fallback    */
+} fslbm_bc_variant;
+
+/* Storage of the PDFs; arithmetic is FP64 for FSLBM_FP64 and FP32 otherwise.
+ * Fill level, mass, excess mass and bubble volumes are always FP64.
+ * FP16S / BF16S store the shifted deviation f_i - w_i. */
+typedef enum {
+  FSLBM_FP64 = 0,
+  FSLBM_FP32 = 1,
+  FSLBM_FP16S = 2,
+  FSLBM_BF16S = 3
+} fslbm_precision;
+
+typedef struct {
+  int nx, ny, nz;     /* cells per axis, each >= 1                             */
+  int periodic[3];    /* nonzero: periodic axis; zero: no-slip walls outside  */
+} fslbm_domain;
+
+typedef struct {
+  double omega;       /* relaxation rate 1/tau, 0 < omega < 2 (Eq. nm-lbm-viscosity) */
+  double trt_magic;   /* TRT magic parameter Lambda (3/16 recommended)          */
+  double g[3];        /* gravitational acceleration; F = rho g (Sec. 2.2)       */
+  double sigma;       /* surface tension (Eq. nm-fslbm-pressure-laplace)        */
+  double eps_phi;     /* conversion threshold epsilon_phi, paper: 1e-2          */
+  double p_v0;        /* initial volume pressure p^V(0), paper: p0 = 1/3        */
+  int precision;      /* fslbm_precision                                        */
+  int om3_fallback;   /* FSLBM_NBKC (paper's text) or FSLBM_NBRC (its equation) */
+  int bubble_model;   /* 0: all gas at p_v0; 1: per-bubble volume tracking
+                         (Eq. nm-fslbm-pressure-volume)                         */
+  void* stream;       /* cudaStream_t for all work, NULL = default stream       */
+} fslbm_params;
+
+/* Whole-domain observables (FP64 reductions on the device). */
+typedef struct {
+  int64_t step;        /* steps done since init                              */
+  double total_mass;   /* sum rho (liquid) + sum m (interface), Eq. nm-fslbm-mass */
+  int64_t n_liquid, n_interface, n_gas, n_obstacle;
+  double max_u;        /* max |u| over liquid and interface cells            */
+  int nan_seen;        /* a non-finite value or rho <= 0 was seen            */
+  int n_bubbles;       /* bubbles tracked (connected gas regions at init)    */
+  double liquid_volume;/* sum of fill levels over liquid and interface cells */
+} fslbm_obs;
+
+/* Defaults: omega 1, Lambda 3/16, g 0, sigma 0, eps_phi 1e-2, p_v0 1/3,
+ * FP32, OM3 fallback NBKC, no bubble model, default stream. */
+void fslbm_params_default(fslbm_params* p);
+
+/* Create a context for one domain (Sec. 2; Sec. 3 for bc_variant).
+ * Allocates all device memory for the domain; returns FSLBM_EINVAL for bad
+ * sizes/enums (out untouched), FSLBM_ENOMEM if the device is full. */
+fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
+                          fslbm_collision collision, fslbm_bc_variant bc_variant,
+                          const fslbm_params* params, fslbm_ctx** out);
+
+/* Initial state (Sec. 2.2).  fill[N] fill levels (used on interface cells;
+ * liquid 1, gas 0), flags[N] cell types 0..3, velocity[3N] component-major
+ * (ux[N], uy[N], uz[N]) or NULL for rest, density[N] or NULL for rho = 1.
+ * PDFs start at f^eq(rho, u) (Eq. nm-lbm-equilibrium); mass m = phi rho
+ * (Eq. nm-fslbm-mass).  Gas bubbles are the connected gas regions, labelled
+ * in the order of their lowest cell index.  Host pointers, copied.
+ * FSLBM_EINVAL if a flag is > 3 or a liquid cell touches a gas cell (the
+ * interface layer must be closed). */
+fslbm_status fslbm_init(fslbm_ctx* ctx, const double* fill, const uint8_t* flags,
+                        const double* velocity, const double* density);
+
+/* Advance n >= 0 time steps: geometry (K8 smoothing, Parker-Youngs normal,
+ * FDM curvature), stream-collide with the free-surface BC of the chosen
+ * variant, mass exchange and fill update, conversion with neighbour fix-up,
+ * excess-mass redistribution and the bubble-pressure update (Sec. 2.2, 3).
+ * Asynchronous on params.stream; launch errors are returned, device-side
+ * instability is reported by fslbm_sync / fslbm_observables. */
+fslbm_status fslbm_step(fslbm_ctx* ctx, int n);
+
+/* Wait for the stream; FSLBM_EUNSTABLE if an instability was flagged,
+ * FSLBM_ECAPACITY if the interface band overflowed. */
+fslbm_status fslbm_sync(fslbm_ctx* ctx);
+
+/* Whole-domain observables; synchronizes.  Returns FSLBM_EUNSTABLE (with
+ * *out filled) when max |u| >= c_s or a NaN was seen. */
+fslbm_status fslbm_observables(fslbm_ctx* ctx, fslbm_obs* out);
+
+/* Copy fields to host buffers (any pointer may be NULL); synchronizes.
+ * pdf[q*N] direction-major post-collision PDFs as FP64, fill[N], flags[N]
+ * (0..3), mass[N] (meaningful on interface cells; 0 on gas). */
+fslbm_status fslbm_read_fields(fslbm_ctx* ctx, double* pdf, double* fill,
+                               uint8_t* flags, double* mass);
+
+/* Per-bubble volume V_b and volume pressure p^V_b (Eq. nm-fslbm-pressure-volume);
+ * writes min(cap, n) entries, *n_out = number of bubbles.  Synchronizes. */
+fslbm_status fslbm_bubbles(fslbm_ctx* ctx, double* volume, double* pressure,
+                           int cap, int* n_out);
+
+/* Opt-in per-stage CUDA-event timing of the next steps (0 disables).  While
+ * enabled, fslbm_step launches kernels one by one (no CUDA graph). */
+fslbm_status fslbm_set_timing(fslbm_ctx* ctx, int enable);
+/* Accumulated milliseconds per stage since timing was enabled, in the order
+ * geometry, bulk, interface, convert, bubbles; writes min(cap, 5) values. */
+fslbm_status fslbm_stage_times(fslbm_ctx* ctx, double* ms, int cap, int* n_launches);
+
+/* Checkpoint of the full state (PDFs, flags, fill, mass, bubbles, step) into
+ * a caller buffer.  With buf == NULL only *size is returned. */
+fslbm_status fslbm_save(fslbm_ctx* ctx, void* buf, size_t* size);
+fslbm_status fslbm_load(fslbm_ctx* ctx, const void* buf, size_t size);
+
+/* Number of interface cells of the current state (synchronizes). */
+fslbm_status fslbm_interface_count(fslbm_ctx* ctx, int64_t* n);
+
+/* Sizes of the work lists of the next step (synchronizes; any pointer may be
+ * NULL): interface cells, 32-cell segments swept by the bulk kernel (those
+ * that hold or held liquid) and 8^3 geometry tiles holding interface cells. */
+fslbm_status fslbm_work_counts(fslbm_ctx* ctx, int64_t* interface_cells,
+                               int64_t* liquid_segments, int64_t* geometry_tiles);
+
+void fslbm_destroy(fslbm_ctx* ctx);
+const char* fslbm_last_error(const fslbm_ctx* ctx);
+const char* fslbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSLBM_H */

@@ -1,0 +1,730 @@
+// C ABI of the FSLBM library (include/fslbm.h): context management, initial
+// state, CUDA-graph step driver, observables, field readback, checkpoints.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fslbm.h"
+#include "fslbm_internal.h"
+#include "fslbm_kernels.cuh"
+
+using namespace fslbm;
+
+struct fslbm_ctx {
+  fslbm_domain dom;
+  int q = 19, collision = 1, variant = 3;
+  fslbm_params prm;
+  KParams kp;
+  DPtrs d;
+  Ops ops;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  Fork fork{nullptr, nullptr, nullptr};
+  int bulk_grid = 608;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int parity = 0;
+  int64_t step = 0;
+  bool initialized = false;
+  int band_grid = 608;
+  bool timing = false;
+  StageEvents ev;
+  bool ev_made = false;
+  double stage_ms[5] = {0, 0, 0, 0, 0};
+  long long launches = 0;
+  double* d_obs = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+const char* kVersion = "fslbm-gb300 1.0";
+
+fslbm_status fail(fslbm_ctx* c, fslbm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+fslbm_status cuda_fail(fslbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? FSLBM_ENOMEM : FSLBM_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dalloc(fslbm_ctx* c, T** p, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) {
+    c->allocs.push_back(v);
+    *p = (T*)v;
+  }
+  return e;
+}
+
+void dfree(fslbm_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) {
+      cudaFree(p);
+      c->allocs.erase(c->allocs.begin() + (long)i);
+      return;
+    }
+}
+
+void destroy_graphs(fslbm_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) {
+      cudaGraphExecDestroy(c->graph[i]);
+      c->graph[i] = nullptr;
+    }
+}
+
+cudaError_t build_graphs(fslbm_ctx* c) {
+  destroy_graphs(c);
+  for (int par = 0; par < 2; ++par) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    c->ops.step(c->d, c->kp, par, c->band_grid, c->bulk_grid, c->cap_stream, nullptr, &c->fork);
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&c->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int launches_per_step(const fslbm_ctx* c) {
+  return 7 + ((c->kp.bubble_model && c->d.nb > 0) ? 1 : 0);
+}
+
+// Host labelling of connected gas regions in the order of their lowest cell
+// index (lattice neighbourhood, periodic wrap); interface cells take the
+// lowest label of their gas neighbours.
+void label_bubbles(const fslbm_ctx* c, const uint8_t* flags, std::vector<int>& bid, int& nb) {
+  const int nx = c->dom.nx, ny = c->dom.ny, nz = c->dom.nz;
+  const long long N = (long long)nx * ny * nz;
+  bid.assign((size_t)N, -1);
+  std::vector<int> stack;
+  auto nbr = [&](int x, int y, int z, int dx, int dy, int dz) -> long long {
+    int X = x + dx, Y = y + dy, Z = z + dz;
+    if (X < 0 || X >= nx) {
+      if (!c->dom.periodic[0]) return -1;
+      X = (X % nx + nx) % nx;
+    }
+    if (Y < 0 || Y >= ny) {
+      if (!c->dom.periodic[1]) return -1;
+      Y = (Y % ny + ny) % ny;
+    }
+    if (Z < 0 || Z >= nz) {
+      if (!c->dom.periodic[2]) return -1;
+      Z = (Z % nz + nz) % nz;
+    }
+    return (long long)X + (long long)nx * (Y + (long long)ny * Z);
+  };
+  nb = 0;
+  for (long long s = 0; s < N; ++s) {
+    if (flags[s] != T_GAS || bid[s] >= 0) continue;
+    bid[s] = nb;
+    stack.push_back((int)s);
+    while (!stack.empty()) {
+      const int a = stack.back();
+      stack.pop_back();
+      const int x = a % nx, y = (a / nx) % ny, z = a / (nx * ny);
+      for (int i = 1; i < c->q; ++i) {
+        const long long n = nbr(x, y, z, CX(i), CY(i), CZ(i));
+        if (n >= 0 && flags[n] == T_GAS && bid[n] < 0) {
+          bid[n] = nb;
+          stack.push_back((int)n);
+        }
+      }
+    }
+    ++nb;
+  }
+  for (long long s = 0; s < N; ++s) {
+    if (flags[s] != T_IFACE) continue;
+    const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+    int best = -1;
+    for (int i = 1; i < c->q; ++i) {
+      const long long n = nbr(x, y, z, CX(i), CY(i), CZ(i));
+      if (n >= 0 && flags[n] == T_GAS && (best < 0 || bid[n] < best)) best = bid[n];
+    }
+    bid[s] = best;
+  }
+}
+
+bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
+
+}  // namespace
+
+extern "C" {
+
+const char* fslbm_version(void) { return kVersion; }
+
+void fslbm_params_default(fslbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->omega = 1.0;
+  p->trt_magic = 3.0 / 16.0;
+  p->eps_phi = 1e-2;
+  p->p_v0 = 1.0 / 3.0;
+  p->precision = FSLBM_FP32;
+  p->om3_fallback = FSLBM_NBKC;
+  p->bubble_model = 0;
+  p->stream = nullptr;
+}
+
+const char* fslbm_last_error(const fslbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
+                          fslbm_collision collision, fslbm_bc_variant bc_variant,
+                          const fslbm_params* params, fslbm_ctx** out) {
+  if (!domain || !params || !out) return FSLBM_EINVAL;
+  if (domain->nx < 1 || domain->ny < 1 || domain->nz < 1) return FSLBM_EINVAL;
+  const long long N = (long long)domain->nx * domain->ny * domain->nz;
+  if (N > 400LL * 1000 * 1000) return FSLBM_EINVAL;
+  if (lattice != FSLBM_D3Q19 && lattice != FSLBM_D3Q27) return FSLBM_EINVAL;
+  if (!valid_enum(collision, 0, 1) || !valid_enum(bc_variant, 1, 4)) return FSLBM_EINVAL;
+  if (!valid_enum(params->precision, 0, 3)) return FSLBM_EINVAL;
+  if (params->om3_fallback != FSLBM_NBRC && params->om3_fallback != FSLBM_NBKC) return FSLBM_EINVAL;
+  if (!(params->omega > 0.0 && params->omega < 2.0)) return FSLBM_EINVAL;
+  if (collision == FSLBM_TRT && !(params->trt_magic > 0.0)) return FSLBM_EINVAL;
+  if (!(params->eps_phi >= 0.0) || !(params->p_v0 > 0.0)) return FSLBM_EINVAL;
+
+  fslbm_ctx* c = new (std::nothrow) fslbm_ctx();
+  if (!c) return FSLBM_ENOMEM;
+  c->dom = *domain;
+  c->q = (int)lattice;
+  c->collision = (int)collision;
+  c->variant = (int)bc_variant;
+  c->prm = *params;
+  c->stream = (cudaStream_t)params->stream;
+  switch (params->precision) {
+    case FSLBM_FP64: c->ops = ops_f64(c->q); break;
+    case FSLBM_FP32: c->ops = ops_f32(c->q); break;
+    case FSLBM_FP16S: c->ops = ops_f16s(c->q); break;
+    default: c->ops = ops_bf16s(c->q); break;
+  }
+  KParams& k = c->kp;
+  k.nx = domain->nx;
+  k.ny = domain->ny;
+  k.nz = domain->nz;
+  for (int a = 0; a < 3; ++a) k.per[a] = domain->periodic[a] ? 1 : 0;
+  k.N = (int)N;
+  k.Np = (N + 63) / 64 * 64;
+  k.omega = params->omega;
+  if (collision == FSLBM_TRT) {
+    k.om_m = 1.0 / (0.5 + params->trt_magic / (1.0 / params->omega - 0.5));
+  } else {
+    k.om_m = params->omega;
+  }
+  k.pref_p = 1.0 - 0.5 * k.omega;
+  k.pref_m = 1.0 - 0.5 * k.om_m;
+  for (int a = 0; a < 3; ++a) k.g[a] = params->g[a];
+  k.sigma = params->sigma;
+  k.eps = params->eps_phi;
+  k.pv0 = params->p_v0;
+  k.divx = make_fastdiv((unsigned)k.nx);
+  k.divy = make_fastdiv((unsigned)k.ny);
+  for (int i = 0; i < 27; ++i) {
+    k.off[i] = CX(i) + k.nx * (CY(i) + k.ny * CZ(i));
+    k.dofs[i] = (long long)i * k.Np - k.off[i];
+  }
+  k.variant = (int)bc_variant;
+  k.om3_fb = params->om3_fallback;
+  k.bubble_model = params->bubble_model ? 1 : 0;
+  k.collision = (int)collision;
+
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
+  c->band_grid = sms * 2;
+  c->bulk_grid = sms * (params->precision == FSLBM_FP64 ? 2 : 4);
+
+  DPtrs& d = c->d;
+  std::memset(&d, 0, sizeof(d));
+  const size_t n4 = (size_t)((N + 3) / 4 * 4);
+  cudaError_t e = cudaSuccess;
+  const size_t pdf_bytes = (size_t)c->q * (size_t)k.Np * c->ops.elem_size;
+  const size_t rs = c->ops.real_size;
+#define ALLOC(ptr, bytes)                                 \
+  if (e == cudaSuccess) e = dalloc(c, &(ptr), (bytes));
+  ALLOC(d.pdf[0], pdf_bytes);
+  ALLOC(d.pdf[1], pdf_bytes);
+  ALLOC(d.flags, n4);
+  ALLOC(d.wallmask, N * sizeof(uint32_t));
+  ALLOC(d.phi, N * sizeof(double));
+  ALLOC(d.mass, N * sizeof(double));
+  ALLOC(d.bid, N * sizeof(int));
+  ALLOC(d.cls, n4);
+  ALLOC(d.mark, n4);
+  ALLOC(d.conv, n4);
+  ALLOC(d.cfin, n4);
+  ALLOC(d.claim, n4);
+  ALLOC(d.share, N * sizeof(double));
+  ALLOC(d.band[0], N * sizeof(int));
+  ALLOC(d.band[1], N * sizeof(int));
+  ALLOC(d.counts, 8 * sizeof(int));
+  const long long ntiles = (long long)((domain->nx + 7) / 8) * ((domain->ny + 7) / 8) * ((domain->nz + 7) / 8);
+  ALLOC(d.tiles[0], ntiles * sizeof(int));
+  ALLOC(d.tiles[1], ntiles * sizeof(int));
+  ALLOC(d.tile_mark, ntiles * sizeof(int));
+  const long long nseg = (N + 31) / 32;
+  ALLOC(d.segs, nseg * sizeof(int));
+  ALLOC(d.seg_mark, nseg * sizeof(int));
+  ALLOC(d.newlist, N * sizeof(int));
+  ALLOC(d.nhat, 3 * N * rs);
+  ALLOC(d.rhog, N * rs);
+  ALLOC(d.m_next, N * sizeof(double));
+  ALLOC(d.phi_next, N * sizeof(double));
+  ALLOC(d.rho_band, N * sizeof(double));
+  ALLOC(d.err, 4 * sizeof(int));
+  d.red_blocks = sms * 2;
+  ALLOC(d.red, (size_t)d.red_blocks * kObsFields * sizeof(double));
+  ALLOC(c->d_obs, kObsFields * sizeof(double));
+#undef ALLOC
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->fork.side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.claim, 0, n4, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.tile_mark, 0, ntiles * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    fslbm_status s = e == cudaErrorMemoryAllocation ? FSLBM_ENOMEM : FSLBM_ECUDA;
+    cudaGetLastError();
+    fslbm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return FSLBM_OK;
+}
+
+void fslbm_destroy(fslbm_ctx* c) {
+  if (!c) return;
+  if (c->stream || c->cap_stream) cudaStreamSynchronize(c->stream);
+  destroy_graphs(c);
+  if (c->ev_made)
+    for (int i = 0; i < StageEvents::kMarks; ++i) cudaEventDestroy(c->ev.ev[i]);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->fork.side) cudaStreamDestroy(c->fork.side);
+  if (c->fork.fork) cudaEventDestroy(c->fork.fork);
+  if (c->fork.join) cudaEventDestroy(c->fork.join);
+  delete c;
+}
+
+fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
+                        const double* velocity, const double* density) {
+  if (!c) return FSLBM_EINVAL;
+  if (!fill || !flags) return fail(c, FSLBM_EINVAL, "fill and flags are required");
+  const size_t N = (size_t)c->kp.N;
+  for (size_t i = 0; i < N; ++i)
+    if (flags[i] > 3) return fail(c, FSLBM_EINVAL, "flag value > 3");
+  cudaStream_t st = c->stream;
+  uint8_t* raw = nullptr;
+  double *dfill = nullptr, *dvel = nullptr, *dden = nullptr;
+  int* bad = nullptr;
+  cudaError_t e = dalloc(c, &raw, N);
+  if (e == cudaSuccess) e = dalloc(c, &dfill, N * sizeof(double));
+  if (e == cudaSuccess && velocity) e = dalloc(c, &dvel, 3 * N * sizeof(double));
+  if (e == cudaSuccess && density) e = dalloc(c, &dden, N * sizeof(double));
+  if (e == cudaSuccess) e = dalloc(c, &bad, sizeof(int));
+  auto cleanup = [&]() {
+    dfree(c, raw);
+    dfree(c, dfill);
+    dfree(c, dvel);
+    dfree(c, dden);
+    dfree(c, bad);
+  };
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw, flags, N, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dfill, fill, N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && velocity)
+    e = cudaMemcpyAsync(dvel, velocity, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && density)
+    e = cudaMemcpyAsync(dden, density, N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+  int hbad = 0;
+  if (e == cudaSuccess) {
+    c->ops.init_check(c->kp, raw, bad, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(c, e, "fslbm_init upload");
+  }
+  if (hbad) {
+    cleanup();
+    return fail(c, FSLBM_EINVAL,
+                (hbad & 2) ? "a liquid cell touches a gas cell (interface layer not closed)"
+                           : "flag value > 3");
+  }
+  // bubbles (host labelling, fixed-point initial volumes)
+  std::vector<int> bid;
+  int nb = 0;
+  std::vector<double> V0;
+  std::vector<long long> gas;
+  if (c->kp.bubble_model) {
+    label_bubbles(c, flags, bid, nb);
+    std::vector<long long> acc((size_t)(nb > 0 ? nb : 1), 0);
+    gas.assign((size_t)(nb > 0 ? nb : 1), 0);
+    for (size_t s = 0; s < N; ++s) {
+      const int b = bid[s];
+      if (b < 0) continue;
+      if (flags[s] == T_GAS) {
+        acc[b] += 4294967296LL;
+        gas[b] += 1;
+      } else if (flags[s] == T_IFACE) {
+        acc[b] += (long long)llrint((1.0 - fill[s]) * 4294967296.0);
+      }
+    }
+    V0.resize((size_t)(nb > 0 ? nb : 1));
+    for (int b = 0; b < nb; ++b) V0[b] = (double)acc[b] / 4294967296.0;
+  }
+  DPtrs& d = c->d;
+  dfree(c, d.V0);
+  dfree(c, d.pV);
+  dfree(c, d.gas_cnt);
+  dfree(c, d.iface_fix);
+  dfree(c, d.Vcur);
+  d.V0 = d.pV = d.Vcur = nullptr;
+  d.gas_cnt = d.iface_fix = nullptr;
+  d.nb = nb;
+  const size_t nbb = (size_t)(nb > 0 ? nb : 1);
+  if (e == cudaSuccess) e = dalloc(c, &d.V0, nbb * sizeof(double));
+  if (e == cudaSuccess) e = dalloc(c, &d.pV, nbb * sizeof(double));
+  if (e == cudaSuccess) e = dalloc(c, &d.gas_cnt, nbb * sizeof(long long));
+  if (e == cudaSuccess) e = dalloc(c, &d.iface_fix, nbb * sizeof(long long));
+  if (e == cudaSuccess) e = dalloc(c, &d.Vcur, nbb * sizeof(double));
+  if (e == cudaSuccess) {
+    std::vector<double> pv(nbb, c->kp.pv0);
+    if (nb > 0) {
+      e = cudaMemcpy(d.V0, V0.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d.Vcur, V0.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d.pV, pv.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d.gas_cnt, gas.data(), nb * sizeof(long long), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemset(d.iface_fix, 0, nb * sizeof(long long));
+    }
+  }
+  if (e == cudaSuccess) {
+    if (c->kp.bubble_model)
+      e = cudaMemcpyAsync(d.bid, bid.data(), N * sizeof(int), cudaMemcpyHostToDevice, st);
+    else
+      e = cudaMemsetAsync(d.bid, 0xff, N * sizeof(int), st);
+  }
+  if (e == cudaSuccess) {
+    c->ops.init_cells(d, c->kp, raw, dfill, dvel, dden, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.counts, 0, 8 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_compact_full<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, st>>>(d.flags, c->kp.N, d.band[0],
+                                                                      &d.counts[0]);
+    k_tiles_of_band<<<c->band_grid, kBlock, 0, st>>>(d, c->kp, 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.seg_mark, 0, (size_t)((N + 31) / 32) * sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_segs_init<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, st>>>(d, c->kp);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_init");
+  c->parity = 0;
+  c->step = 0;
+  c->initialized = true;
+  e = build_graphs(c);
+  if (e != cudaSuccess) {
+    c->initialized = false;
+    return cuda_fail(c, e, "graph capture");
+  }
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_step(fslbm_ctx* c, int n) {
+  if (!c) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "step before init");
+  if (n < 0) return fail(c, FSLBM_EINVAL, "negative step count");
+  for (int s = 0; s < n; ++s) {
+    cudaError_t e;
+    if (c->timing) {
+      c->ops.step(c->d, c->kp, c->parity, c->band_grid, c->bulk_grid, c->stream, &c->ev, nullptr);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventSynchronize(c->ev.ev[StageEvents::kMarks - 1]);
+      if (e == cudaSuccess) {
+        const int map[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
+        for (int k = 0; k < 5; ++k) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, c->ev.ev[map[k][0]], c->ev.ev[map[k][1]]);
+          c->stage_ms[k] += ms;
+        }
+      }
+    } else {
+      e = cudaGraphLaunch(c->graph[c->parity], c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_step");
+    c->launches += launches_per_step(c);
+    c->parity ^= 1;
+    c->step += 1;
+  }
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_sync(fslbm_ctx* c) {
+  if (!c) return FSLBM_EINVAL;
+  int herr[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(herr, c->d.err, sizeof(herr), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_sync");
+  if (herr[0]) return fail(c, FSLBM_EUNSTABLE, "instability: |u|^2 >= c_s^2, rho <= 0 or NaN");
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_observables(fslbm_ctx* c, fslbm_obs* out) {
+  if (!c || !out) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "observables before init");
+  double h[kObsFields];
+  c->ops.observables(c->d, c->kp, c->parity, c->d_obs, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, c->d_obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_observables");
+  std::memset(out, 0, sizeof(*out));
+  out->step = c->step;
+  out->total_mass = h[0];
+  out->max_u = h[1];
+  out->liquid_volume = h[2];
+  out->nan_seen = h[3] != 0.0;
+  out->n_gas = (int64_t)llround(h[4]);
+  out->n_interface = (int64_t)llround(h[5]);
+  out->n_liquid = (int64_t)llround(h[6]);
+  out->n_obstacle = (int64_t)llround(h[7]);
+  out->n_bubbles = c->d.nb;
+  fslbm_status s = fslbm_sync(c);
+  if (s != FSLBM_OK) return s;
+  if (out->nan_seen || !(out->max_u < std::sqrt(1.0 / 3.0)))
+    return fail(c, FSLBM_EUNSTABLE, "instability: max |u| >= c_s or NaN");
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_read_fields(fslbm_ctx* c, double* pdf, double* fill, uint8_t* flags,
+                               double* mass) {
+  if (!c) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "read before init");
+  const size_t N = (size_t)c->kp.N;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (pdf) {
+    double* tmp = nullptr;
+    e = dalloc(c, &tmp, (size_t)c->q * N * sizeof(double));
+    if (e == cudaSuccess) {
+      c->ops.pdf_out(c->d, c->kp, c->parity, tmp, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(pdf, tmp, (size_t)c->q * N * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(c, tmp);
+  }
+  if (e == cudaSuccess && fill)
+    e = cudaMemcpyAsync(fill, c->d.phi, N * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && mass)
+    e = cudaMemcpyAsync(mass, c->d.mass, N * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, c->d.flags, N, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_read_fields");
+  if (flags)
+    for (size_t i = 0; i < N; ++i) flags[i] &= F_TYPE;
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_bubbles(fslbm_ctx* c, double* volume, double* pressure, int cap, int* n_out) {
+  if (!c) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "bubbles before init");
+  const int nb = c->d.nb;
+  if (n_out) *n_out = nb;
+  const int m = nb < cap ? nb : cap;
+  if (m <= 0) return FSLBM_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && pressure)
+    e = cudaMemcpy(pressure, c->d.pV, m * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && volume)
+    e = cudaMemcpy(volume, c->d.Vcur, m * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_bubbles");
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_set_timing(fslbm_ctx* c, int enable) {
+  if (!c) return FSLBM_EINVAL;
+  if (enable && !c->ev_made) {
+    for (int i = 0; i < StageEvents::kMarks; ++i) {
+      cudaError_t e = cudaEventCreate(&c->ev.ev[i]);
+      if (e != cudaSuccess) return cuda_fail(c, e, "event create");
+    }
+    c->ev_made = true;
+  }
+  c->timing = enable != 0;
+  for (int k = 0; k < 5; ++k) c->stage_ms[k] = 0.0;
+  c->launches = 0;
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_stage_times(fslbm_ctx* c, double* ms, int cap, int* n_launches) {
+  if (!c) return FSLBM_EINVAL;
+  for (int k = 0; k < 5 && k < cap; ++k) ms[k] = c->stage_ms[k];
+  if (n_launches) *n_launches = (int)c->launches;
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_interface_count(fslbm_ctx* c, int64_t* n) {
+  if (!c || !n) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "before init");
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, &c->d.counts[c->parity], sizeof(int), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "interface count");
+  *n = h;
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_work_counts(fslbm_ctx* c, int64_t* interface_cells, int64_t* liquid_segments,
+                               int64_t* geometry_tiles) {
+  if (!c) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "before init");
+  int h[8];
+  cudaError_t e = cudaMemcpyAsync(h, c->d.counts, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "work counts");
+  if (interface_cells) *interface_cells = h[c->parity];
+  if (liquid_segments) *liquid_segments = h[5];
+  if (geometry_tiles) *geometry_tiles = h[3 + c->parity];
+  return FSLBM_OK;
+}
+
+// ------------------------------------------------------------ checkpoints
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int nx, ny, nz, q, precision, nb;
+  int64_t step;
+  int64_t pdf_bytes;
+};
+}  // namespace
+
+fslbm_status fslbm_save(fslbm_ctx* c, void* buf, size_t* size) {
+  if (!c || !size) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "save before init");
+  const size_t N = (size_t)c->kp.N;
+  const size_t nb = (size_t)c->d.nb;
+  const size_t pdf_bytes = (size_t)c->q * (size_t)c->kp.Np * c->ops.elem_size;
+  const size_t need = sizeof(CkptHeader) + pdf_bytes + N + 2 * N * sizeof(double) +
+                      N * sizeof(int) + nb * (3 * sizeof(double) + sizeof(long long));
+  if (!buf) {
+    *size = need;
+    return FSLBM_OK;
+  }
+  if (*size < need) return fail(c, FSLBM_EINVAL, "checkpoint buffer too small");
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "FSLBMCK1", 8);
+  h.nx = c->kp.nx;
+  h.ny = c->kp.ny;
+  h.nz = c->kp.nz;
+  h.q = c->q;
+  h.precision = c->prm.precision;
+  h.nb = (int)nb;
+  h.step = c->step;
+  h.pdf_bytes = (int64_t)pdf_bytes;
+  char* p = (char*)buf;
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  auto d2h = [&](const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(p, src, bytes, cudaMemcpyDeviceToHost);
+    p += bytes;
+  };
+  d2h(c->d.pdf[c->parity], pdf_bytes);
+  d2h(c->d.flags, N);
+  d2h(c->d.phi, N * sizeof(double));
+  d2h(c->d.mass, N * sizeof(double));
+  d2h(c->d.bid, N * sizeof(int));
+  d2h(c->d.V0, nb * sizeof(double));
+  d2h(c->d.pV, nb * sizeof(double));
+  d2h(c->d.Vcur, nb * sizeof(double));
+  d2h(c->d.gas_cnt, nb * sizeof(long long));
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_save");
+  *size = need;
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_load(fslbm_ctx* c, const void* buf, size_t size) {
+  if (!c || !buf) return FSLBM_EINVAL;
+  if (!c->initialized) return fail(c, FSLBM_ESTATE, "load needs an initialised context");
+  if (size < sizeof(CkptHeader)) return fail(c, FSLBM_EINVAL, "checkpoint too small");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const size_t N = (size_t)c->kp.N;
+  const size_t pdf_bytes = (size_t)c->q * (size_t)c->kp.Np * c->ops.elem_size;
+  if (std::memcmp(h.magic, "FSLBMCK1", 8) != 0 || h.nx != c->kp.nx || h.ny != c->kp.ny ||
+      h.nz != c->kp.nz || h.q != c->q || h.precision != c->prm.precision || h.nb != c->d.nb ||
+      h.pdf_bytes != (int64_t)pdf_bytes)
+    return fail(c, FSLBM_EINVAL, "checkpoint does not match this context");
+  const size_t nb = (size_t)h.nb;
+  const size_t need = sizeof(CkptHeader) + pdf_bytes + N + 2 * N * sizeof(double) +
+                      N * sizeof(int) + nb * (3 * sizeof(double) + sizeof(long long));
+  if (size < need) return fail(c, FSLBM_EINVAL, "checkpoint truncated");
+  const char* p = (const char*)buf + sizeof(h);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  auto h2d = [&](void* dst, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice);
+    p += bytes;
+  };
+  h2d(c->d.pdf[0], pdf_bytes);
+  h2d(c->d.flags, N);
+  h2d(c->d.phi, N * sizeof(double));
+  h2d(c->d.mass, N * sizeof(double));
+  h2d(c->d.bid, N * sizeof(int));
+  h2d(c->d.V0, nb * sizeof(double));
+  h2d(c->d.pV, nb * sizeof(double));
+  h2d(c->d.Vcur, nb * sizeof(double));
+  h2d(c->d.gas_cnt, nb * sizeof(long long));
+  if (e == cudaSuccess && nb) e = cudaMemset(c->d.iface_fix, 0, nb * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d.counts, 0, 8 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d.err, 0, 4 * sizeof(int), c->stream);
+  if (e == cudaSuccess) {
+    const size_t nt = (size_t)((c->kp.nx + 7) / 8) * ((c->kp.ny + 7) / 8) * ((c->kp.nz + 7) / 8);
+    e = cudaMemsetAsync(c->d.tile_mark, 0, nt * sizeof(int), c->stream);
+  }
+  if (e == cudaSuccess) {
+    k_compact_full<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(c->d.flags, c->kp.N,
+                                                                             c->d.band[0], &c->d.counts[0]);
+    k_tiles_of_band<<<c->band_grid, kBlock, 0, c->stream>>>(c->d, c->kp, 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d.seg_mark, 0, (size_t)((N + 31) / 32) * sizeof(int), c->stream);
+  if (e == cudaSuccess) {
+    k_segs_init<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(c->d, c->kp);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_load");
+  c->parity = 0;
+  c->step = h.step;
+  return FSLBM_OK;
+}
+
+}  // extern "C"

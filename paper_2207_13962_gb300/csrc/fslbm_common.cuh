@@ -1,0 +1,182 @@
+// Device-side building blocks of the FSLBM step: lattice tables, cell-flag
+// bits, PDF storage formats and the parameter block passed to every kernel.
+//
+// Lattices D3Q19 / D3Q27 of Sec. 2.1 (weights from the standard sets); the
+// direction order is the one documented in include/fslbm.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fslbm {
+
+// ----------------------------------------------------------------- flags
+// bits 0-1: cell type; bit 2: static "a lattice neighbour is an obstacle or
+// lies outside a non-periodic face"; bit 3: static "a lattice neighbour lies
+// across a periodic face" (both computed once at init).
+enum : uint8_t { T_GAS = 0, T_IFACE = 1, T_LIQ = 2, T_OBST = 3 };
+enum : uint8_t { F_TYPE = 3, F_NEAR_WALL = 4, F_WRAP = 8 };
+// Thuerey classes of interface cells.
+enum : uint8_t { CL_STD = 0, CL_NF = 1, CL_NE = 2 };
+// Conversion marks.
+enum : uint8_t { CV_NONE = 0, CV_TOL = 1, CV_TOG = 2, CV_DEFER = 3 };
+
+// ------------------------------------------------------------- lattice
+// Direction i encoded as (cx+1) + 3 (cy+1) + 9 (cz+1).
+__host__ __device__ constexpr int dcode(int i) {
+  return i == 0    ? 13
+         : i == 1  ? 14
+         : i == 2  ? 12
+         : i == 3  ? 16
+         : i == 4  ? 10
+         : i == 5  ? 22
+         : i == 6  ? 4
+         : i == 7  ? 17
+         : i == 8  ? 9
+         : i == 9  ? 11
+         : i == 10 ? 15
+         : i == 11 ? 23
+         : i == 12 ? 3
+         : i == 13 ? 5
+         : i == 14 ? 21
+         : i == 15 ? 25
+         : i == 16 ? 1
+         : i == 17 ? 7
+         : i == 18 ? 19
+         : i == 19 ? 26
+         : i == 20 ? 0
+         : i == 21 ? 8
+         : i == 22 ? 18
+         : i == 23 ? 20
+         : i == 24 ? 6
+         : i == 25 ? 24
+                   : 2;
+}
+__host__ __device__ constexpr int CX(int i) { return dcode(i) % 3 - 1; }
+__host__ __device__ constexpr int CY(int i) { return (dcode(i) / 3) % 3 - 1; }
+__host__ __device__ constexpr int CZ(int i) { return dcode(i) / 9 - 1; }
+__host__ __device__ constexpr int OPP(int i) {
+  return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+}
+__host__ __device__ constexpr int N2(int i) {
+  return CX(i) * CX(i) + CY(i) * CY(i) + CZ(i) * CZ(i);
+}
+
+template <int Q, class R>
+__host__ __device__ constexpr R W(int i) {
+  return Q == 19 ? (N2(i) == 0   ? R(1.0 / 3.0)
+                    : N2(i) == 1 ? R(1.0 / 18.0)
+                                 : R(1.0 / 36.0))
+                 : (N2(i) == 0   ? R(8.0 / 27.0)
+                    : N2(i) == 1 ? R(2.0 / 27.0)
+                    : N2(i) == 2 ? R(1.0 / 54.0)
+                                 : R(1.0 / 216.0));
+}
+
+// -------------------------------------------------------------- storage
+// Real: arithmetic type; T: stored type; load/store convert with the
+// shift f - w_i for the 16-bit formats.
+struct StoreF64 {
+  using T = double;
+  using Real = double;
+  static constexpr int code = 0;
+  __device__ static __forceinline__ Real load(T v, Real) { return v; }
+  __device__ static __forceinline__ T store(Real f, Real) { return f; }
+};
+struct StoreF32 {
+  using T = float;
+  using Real = float;
+  static constexpr int code = 1;
+  __device__ static __forceinline__ Real load(T v, Real) { return v; }
+  __device__ static __forceinline__ T store(Real f, Real) { return f; }
+};
+struct StoreF16S {
+  using T = __half;
+  using Real = float;
+  static constexpr int code = 2;
+  __device__ static __forceinline__ Real load(T v, Real w) { return __half2float(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return __float2half_rn(f - w); }
+};
+struct StoreBF16S {
+  using T = __nv_bfloat16;
+  using Real = float;
+  static constexpr int code = 3;
+  __device__ static __forceinline__ Real load(T v, Real w) { return __bfloat162float(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return __float2bfloat16_rn(f - w); }
+};
+
+// ------------------------------------------------- division by invariants
+// Unsigned division of n < 2^31 by a run-time constant d through one
+// multiply-high (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (mulhi(n, m) + n) >> l.
+struct FastDiv {
+  unsigned d, m, l;
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> l; }
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (unsigned)((((1ull << f.l) - d) << 32) / d + 1ull);
+  return f;
+}
+
+// ----------------------------------------------------------- parameters
+struct KParams {
+  FastDiv divx, divy;
+  int off[27];         // cell-index offset of direction i: cx + nx (cy + ny cz)
+  long long dofs[27];  // i * Np - off[i]: pull source of interior cells
+  int nx, ny, nz;
+  int per[3];
+  int N;        // cells
+  long long Np; // padded cells per PDF direction slice
+  double omega, om_m, pref_p, pref_m;  // SRT: pref_p = 1 - omega/2
+  double g[3];
+  double sigma, eps, pv0;
+  int variant, om3_fb, bubble_model, collision;
+};
+
+// Device pointers of one domain.
+struct DPtrs {
+  void* pdf[2];
+  uint8_t* flags;
+  uint32_t* wallmask;  // bit i: the pull source of direction i is an obstacle
+                       // or outside a non-periodic face (static)
+  double* phi;
+  double* mass;
+  int* bid;
+  uint8_t* cls;
+  uint8_t* mark;
+  uint8_t* conv;
+  uint8_t* cfin;
+  uint8_t* claim;
+  double* share;
+  int* band[2];
+  int* counts;   // [0],[1]: band list counts; [2]: new-cell list count;
+                 // [3],[4]: geometry tile list counts; [5]: segment count
+  int* tiles[2]; // geometry tiles (8^3) holding interface cells
+  int* tile_mark;
+  int* segs;     // 32-cell segments (linear index / 32) holding liquid;
+  int* seg_mark; // grows when cells turn liquid, count in counts[5]
+  int* newlist;
+  void* nhat;    // Real[3 * cap]
+  void* rhog;    // Real[cap]
+  double* m_next;
+  double* phi_next;
+  double* rho_band;
+  double* V0;
+  double* pV;
+  double* Vcur;
+  long long* gas_cnt;
+  long long* iface_fix;
+  int nb;
+  int* err;      // [0] instability seen
+  double* red;   // observable partials
+  int red_blocks;
+};
+
+}  // namespace fslbm

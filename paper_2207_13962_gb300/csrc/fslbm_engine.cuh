@@ -1,0 +1,88 @@
+// Host-side launch sequence of one FSLBM step for a given lattice and PDF
+// storage format.  Included by the per-precision translation units, each of
+// which exports one table of entry points (Ops) to the C-ABI layer.
+#pragma once
+
+#include "fslbm_internal.h"
+#include "fslbm_kernels.cuh"
+
+namespace fslbm {
+
+template <int Q, class S>
+struct Engine {
+  static int grid_cells(const KParams& p) { return (p.N + kBlock - 1) / kBlock; }
+
+  static void init_cells(const DPtrs& d, const KParams& p, const uint8_t* raw, const double* fill,
+                         const double* vel, const double* den, cudaStream_t st) {
+    k_init_cells<Q, S><<<grid_cells(p), kBlock, 0, st>>>(raw, fill, vel, den, d, p, 0);
+  }
+  static void init_check(const KParams& p, const uint8_t* raw, int* bad, cudaStream_t st) {
+    k_init_check<Q><<<grid_cells(p), kBlock, 0, st>>>(raw, p, bad);
+  }
+
+  // One step reading pdf[parity], band[parity]; writing the other buffers.
+  // With a Fork (and no stage events) the bulk sweep runs on the side stream
+  // while geometry, interface update and the first conversion passes run on
+  // the main stream; the streams join before k_apply, the first kernel that
+  // reads post-collision PDFs of liquid cells.
+  static void step(const DPtrs& d, const KParams& p, int parity, int band_grid, int bulk_grid,
+                   cudaStream_t st, StageEvents* ev, const Fork* fk) {
+    auto bulk = [&](cudaStream_t s2) {
+      if (p.collision == 0)
+        k_bulk<Q, S, 0><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
+      else
+        k_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
+    };
+    const bool forked = fk && !ev;
+    if (ev) ev->mark(0, st);
+    if (forked) {
+      cudaEventRecord(fk->fork, st);
+      cudaStreamWaitEvent(fk->side, fk->fork, 0);
+      bulk(fk->side);
+      cudaEventRecord(fk->join, fk->side);
+    }
+    k_geometry<Q, S><<<band_grid, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(d, p, parity);
+    if (ev) ev->mark(1, st);
+    if (!forked) bulk(st);
+    if (ev) ev->mark(2, st);
+    if (p.collision == 0)
+      k_interface<Q, S, 0><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+    else
+      k_interface<Q, S, 1><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+    if (ev) ev->mark(3, st);
+    k_resolve<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+    k_count<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+    if (forked) cudaStreamWaitEvent(st, fk->join, 0);
+    k_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+    k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
+    if (ev) ev->mark(4, st);
+    if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
+    if (ev) ev->mark(5, st);
+  }
+
+  static void observables(const DPtrs& d, const KParams& p, int parity, double* out,
+                          cudaStream_t st) {
+    k_obs_partial<Q, S><<<d.red_blocks, kBlock, 0, st>>>(d, p, parity, d.red);
+    k_obs_final<<<1, 32, 0, st>>>(d.red, d.red_blocks, out);
+  }
+
+  static void pdf_out(const DPtrs& d, const KParams& p, int parity, double* out, cudaStream_t st) {
+    k_pdf_out<Q, S><<<grid_cells(p), kBlock, 0, st>>>(d, p, parity, out);
+  }
+
+  static Ops ops() {
+    cudaFuncSetAttribute(k_geometry<Q, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)geometry_smem<typename S::Real>());
+    Ops o;
+    o.init_cells = &init_cells;
+    o.init_check = &init_check;
+    o.step = &step;
+    o.observables = &observables;
+    o.pdf_out = &pdf_out;
+    o.elem_size = sizeof(typename S::T);
+    o.real_size = sizeof(typename S::Real);
+    return o;
+  }
+};
+
+}  // namespace fslbm

@@ -1,0 +1,45 @@
+// Internal interface between the C-ABI layer and the per-precision engines.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fslbm_common.cuh"
+
+namespace fslbm {
+
+// CUDA events between the stages of a step (geometry, bulk, interface,
+// conversion, bubbles) for opt-in per-stage timing.
+struct StageEvents {
+  static constexpr int kMarks = 6;
+  cudaEvent_t ev[kMarks];
+  void mark(int i, cudaStream_t st) { cudaEventRecord(ev[i], st); }
+};
+
+// Side stream and events that let the bulk sweep run concurrently with the
+// interface-band kernels of the same step.
+struct Fork {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+
+struct Ops {
+  void (*init_cells)(const DPtrs&, const KParams&, const uint8_t* raw, const double* fill,
+                     const double* vel, const double* den, cudaStream_t);
+  void (*init_check)(const KParams&, const uint8_t* raw, int* bad, cudaStream_t);
+  void (*step)(const DPtrs&, const KParams&, int parity, int band_grid, int bulk_grid,
+               cudaStream_t, StageEvents*, const Fork*);
+  void (*observables)(const DPtrs&, const KParams&, int parity, double* out, cudaStream_t);
+  void (*pdf_out)(const DPtrs&, const KParams&, int parity, double* out, cudaStream_t);
+  size_t elem_size;
+  size_t real_size;
+};
+
+// Defined in fslbm_f64.cu, fslbm_f32.cu, fslbm_f16.cu.
+Ops ops_f64(int q);
+Ops ops_f32(int q);
+Ops ops_f16s(int q);
+Ops ops_bf16s(int q);
+
+}  // namespace fslbm

@@ -1,0 +1,1042 @@
+// FSLBM step kernels (arXiv 2207.13962, Sec. 2-3), templated on the lattice
+// (Q = 19 / 27) and the PDF storage format S (FP64, FP32, FP16/BF16 shifted).
+//
+// One step, in stream order:
+//   k_geometry   band   K8 smoothing, Parker-Youngs normal, FDM curvature,
+//                       gas density rho^G, Thuerey class
+//   k_bulk       grid   pull stream + bounce-back + collide of liquid cells
+//   k_interface  band   pull, free-surface BC of the chosen variant, mass
+//                       exchange, fill update, collide, conversion marks
+//   k_resolve    band   conflict rule, claims of gas/liquid neighbours
+//   k_count      band   excess-mass receivers, deferral, shares
+//   k_apply      band+new  excess gather, new interface cells' PDFs
+//   k_finalize   band+new  final flags, next interface list, bubble sums
+//   k_bubble     1 block   bubble volume pressure
+// The interface work runs only on the compacted list of interface cells
+// ("band") and on the cells that conversion turns into interface cells.
+// Conversion and excess redistribution are gather-only: each cell computes
+// its own new values from its neighbours, so the flag field is deterministic.
+//
+// In the FP64 instantiation the kernels are compiled without FMA contraction
+// and every expression keeps the association and summation order of the
+// plain CPU oracle, so results agree to the last bit.
+#pragma once
+
+#include "fslbm_common.cuh"
+
+namespace fslbm {
+
+constexpr int kBlock = 256;
+
+// ------------------------------------------------------------ index helpers
+__device__ __forceinline__ int wrapc(int X, int n, int per) {
+  if (X >= 0 && X < n) return X;
+  if (!per) return -1;
+  X %= n;
+  if (X < 0) X += n;
+  return X;
+}
+__device__ __forceinline__ void decode(const KParams& p, int c, int& x, int& y, int& z) {
+  const int t = (int)p.divx.div((unsigned)c);
+  x = c - t * p.nx;
+  z = (int)p.divy.div((unsigned)t);
+  y = t - z * p.ny;
+}
+// neighbour of (x,y,z) at offset (dx,dy,dz); -1 outside a non-periodic face
+__device__ __forceinline__ int nbr(const KParams& p, int x, int y, int z, int dx, int dy,
+                                   int dz) {
+  int X = wrapc(x + dx, p.nx, p.per[0]);
+  int Y = wrapc(y + dy, p.ny, p.per[1]);
+  int Z = wrapc(z + dz, p.nz, p.per[2]);
+  if (X < 0 || Y < 0 || Z < 0) return -1;
+  return X + p.nx * (Y + p.ny * Z);
+}
+__device__ __forceinline__ int ntype(const uint8_t* flags, int n) {
+  return n < 0 ? T_OBST : (flags[n] & F_TYPE);
+}
+
+// warp-aggregated append; every lane of the warp must call it
+__device__ __forceinline__ int warp_append(int* counter, bool pred) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned b = __ballot_sync(0xffffffffu, pred);
+  int base = 0;
+  if (lane == 0 && b) base = atomicAdd(counter, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return pred ? base + __popc(b & ((1u << lane) - 1u)) : -1;
+}
+
+// ---------------------------------------------------------- cell algebra
+// Eq. nm-lbm-equilibrium with c_s^2 = 1/3.
+template <int Q, class R>
+__device__ __forceinline__ R feq_i(int i, R rho, R ux, R uy, R uz) {
+  R cu = R(CX(i)) * ux + R(CY(i)) * uy + R(CZ(i)) * uz;
+  R usq = ux * ux + uy * uy + uz * uz;
+  R t = R(1.0) + R(3.0) * cu;
+  t = t + R(4.5) * cu * cu;
+  t = t - R(1.5) * usq;
+  return W<Q, R>(i) * rho * t;
+}
+// Guo source without its (1 - omega/2) factor (Eq. nm-lbm-force-guo).
+template <int Q, class R>
+__device__ __forceinline__ R guo_i(int i, R ux, R uy, R uz, R Fx, R Fy, R Fz) {
+  R cx = R(CX(i)), cy = R(CY(i)), cz = R(CZ(i));
+  R cu = cx * ux + cy * uy + cz * uz;
+  R cF = cx * Fx + cy * Fy + cz * Fz;
+  R uF = ux * Fx + uy * Fy + uz * Fz;
+  R t = R(3.0) * (cF - uF) + R(9.0) * cu * cF;
+  return W<Q, R>(i) * t;
+}
+// rho = sum f (Eq. nm-lbm-density); j sums in direction order.
+template <int Q, class R>
+__device__ __forceinline__ void sums(const R* f, R& r, R& jx, R& jy, R& jz) {
+  r = R(0.0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) r = r + f[i];
+  jx = R(0.0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (CX(i) != 0) jx = jx + R(CX(i)) * f[i];
+  jy = R(0.0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (CY(i) != 0) jy = jy + R(CY(i)) * f[i];
+  jz = R(0.0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (CZ(i) != 0) jz = jz + R(CZ(i)) * f[i];
+}
+
+// Collision of one cell (Eqs. nm-lbm-collision, nm-lbm-velocity with
+// F = rho g, SRT relaxing towards f^eq, or TRT).  f is overwritten with f*.
+// Returns rho; sets unstable when |u|^2 >= c_s^2, rho <= 0 or NaN.
+template <int Q, class R, int COLL>
+__device__ __forceinline__ R collide(R* f, const KParams& p, bool& unstable) {
+  R rho, jx, jy, jz;
+  sums<Q, R>(f, rho, jx, jy, jz);
+  const R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
+  R ux = jx / rho + R(0.5) * gx;
+  R uy = jy / rho + R(0.5) * gy;
+  R uz = jz / rho + R(0.5) * gz;
+  R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+  R usq = ux * ux + uy * uy + uz * uz;
+  if (!(usq < R(1.0 / 3.0)) || !(rho > R(0.0))) unstable = true;
+  if (COLL == 0) {
+    const R om = R(p.omega), pref = R(p.pref_p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R fe = feq_i<Q, R>(i, rho, ux, uy, uz);
+      R s = guo_i<Q, R>(i, ux, uy, uz, Fx, Fy, Fz);
+      f[i] = f[i] - om * (f[i] - fe) + pref * s;
+    }
+  } else {
+    // TRT on the pairs (i, ibar): the symmetric parts are shared, the
+    // antisymmetric parts change sign (same roundings as a per-i loop).
+    const R omp = R(p.omega), omm = R(p.om_m), prp = R(p.pref_p), prm = R(p.pref_m);
+    {
+      const R fe = feq_i<Q, R>(0, rho, ux, uy, uz);
+      const R sr = guo_i<Q, R>(0, ux, uy, uz, Fx, Fy, Fz);
+      const R fp = R(0.5) * (f[0] + f[0]), fm = R(0.5) * (f[0] - f[0]);
+      const R ep = R(0.5) * (fe + fe), em = R(0.5) * (fe - fe);
+      const R sp = R(0.5) * (sr + sr), sm = R(0.5) * (sr - sr);
+      f[0] = f[0] - omp * (fp - ep) - omm * (fm - em) + prp * sp + prm * sm;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const int j = i + 1;
+      const R fei = feq_i<Q, R>(i, rho, ux, uy, uz), fej = feq_i<Q, R>(j, rho, ux, uy, uz);
+      const R si = guo_i<Q, R>(i, ux, uy, uz, Fx, Fy, Fz), sj = guo_i<Q, R>(j, ux, uy, uz, Fx, Fy, Fz);
+      const R fp = R(0.5) * (f[i] + f[j]);
+      const R ep = R(0.5) * (fei + fej);
+      const R sp = R(0.5) * (si + sj);
+      const R fmi = R(0.5) * (f[i] - f[j]), fmj = R(0.5) * (f[j] - f[i]);
+      const R emi = R(0.5) * (fei - fej), emj = R(0.5) * (fej - fei);
+      const R smi = R(0.5) * (si - sj), smj = R(0.5) * (sj - si);
+      const R oi = f[i] - omp * (fp - ep) - omm * (fmi - emi) + prp * sp + prm * smi;
+      const R oj = f[j] - omp * (fp - ep) - omm * (fmj - emj) + prp * sp + prm * smj;
+      f[i] = oi;
+      f[j] = oj;
+    }
+  }
+  return rho;
+}
+
+// Collision for the FP32 path: the same TRT/SRT with Guo forcing, evaluated
+// per direction pair (i, ibar) from the symmetric and antisymmetric parts of
+// f^eq (w rho (1 + 4.5 (c.u)^2 - 1.5 u.u) and 3 w rho c.u) and of the source.
+// SRT is the case omega- = omega+.  Fewer operations and live registers than
+// the per-direction form that the FP64 path keeps for bitwise parity.
+template <int Q, int COLL>
+__device__ __forceinline__ float collide_fast(float* f, const KParams& p, bool& unstable) {
+  float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rho += f[i];
+    if (CX(i) != 0) jx += float(CX(i)) * f[i];
+    if (CY(i) != 0) jy += float(CY(i)) * f[i];
+    if (CZ(i) != 0) jz += float(CZ(i)) * f[i];
+  }
+  const float gx = float(p.g[0]), gy = float(p.g[1]), gz = float(p.g[2]);
+  const float inv = __frcp_rn(rho);
+  const float ux = jx * inv + 0.5f * gx, uy = jy * inv + 0.5f * gy, uz = jz * inv + 0.5f * gz;
+  const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+  const float usq = ux * ux + uy * uy + uz * uz;
+  if (!(usq < 1.0f / 3.0f) || !(rho > 0.f)) unstable = true;
+  const float omp = float(p.omega), prp = float(p.pref_p);
+  const float omm = COLL == 0 ? omp : float(p.om_m), prm = COLL == 0 ? prp : float(p.pref_m);
+  const float base = 1.0f - 1.5f * usq;
+  const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
+  {
+    const float w = W<Q, float>(0);
+    const float es = w * rho * base;
+    f[0] = f[0] - omp * (f[0] - es) - prp * w * uF3;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int j = i + 1;
+    const float w = W<Q, float>(i);
+    const float cu = float(CX(i)) * ux + float(CY(i)) * uy + float(CZ(i)) * uz;
+    const float cF = float(CX(i)) * Fx + float(CY(i)) * Fy + float(CZ(i)) * Fz;
+    const float es = w * rho * (base + 4.5f * cu * cu);
+    const float ea = 3.0f * w * rho * cu;
+    const float ss = w * (9.0f * cu * cF - uF3);
+    const float sa = 3.0f * w * cF;
+    const float fp = 0.5f * (f[i] + f[j]);
+    const float fm = 0.5f * (f[i] - f[j]);
+    const float A = omp * (fp - es) - prp * ss;
+    const float B = omm * (fm - ea) - prm * sa;
+    const float fi = f[i] - A - B;
+    const float fj = f[j] - A + B;
+    f[i] = fi;
+    f[j] = fj;
+  }
+  return rho;
+}
+
+template <int Q, class S, int COLL>
+__device__ __forceinline__ typename S::Real collide_any(typename S::Real* f, const KParams& p,
+                                                        bool& unstable) {
+  if constexpr (S::code == 0)
+    return collide<Q, double, COLL>(f, p, unstable);
+  else
+    return collide_fast<Q, COLL>(f, p, unstable);
+}
+
+// rho and u of a cell from its post-collision PDFs: rho u = sum c f* - F/2.
+template <int Q, class S>
+__device__ __forceinline__ void post_moments(const typename S::T* P, long long Np, int c,
+                                             const KParams& p, typename S::Real& rho,
+                                             typename S::Real u[3]) {
+  using R = typename S::Real;
+  R f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = S::load(P[(long long)i * Np + c], W<Q, R>(i));
+  R jx, jy, jz;
+  sums<Q, R>(f, rho, jx, jy, jz);
+  u[0] = jx / rho - R(0.5) * R(p.g[0]);
+  u[1] = jy / rho - R(0.5) * R(p.g[1]);
+  u[2] = jz / rho - R(0.5) * R(p.g[2]);
+}
+
+// ------------------------------------------------------------------ init
+// Validates raw flags: values <= 3 and no liquid cell next to a gas cell.
+template <int Q>
+__global__ void k_init_check(const uint8_t* __restrict__ raw, KParams p, int* bad) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  uint8_t t = raw[c];
+  if (t > 3) {
+    atomicOr(bad, 1);
+    return;
+  }
+  if (t != T_LIQ) return;
+  int x, y, z;
+  decode(p, c, x, y, z);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    int n = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+    if (n >= 0 && raw[n] == T_GAS) atomicOr(bad, 2);
+  }
+}
+
+// Initial fields: phi, m = phi rho (Eq. nm-fslbm-mass), f = f^eq(rho, u).
+template <int Q, class S>
+__global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __restrict__ fill,
+                             const double* __restrict__ vel, const double* __restrict__ den,
+                             DPtrs d, KParams p, int parity) {
+  using R = typename S::Real;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const uint8_t t = raw[c];
+  int x, y, z;
+  decode(p, c, x, y, z);
+  uint8_t fl = t;
+  uint32_t wm = 0u;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    int n = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+    if (n < 0 || raw[n] == T_OBST) fl |= F_NEAR_WALL;
+    const int X = x + CX(i), Y = y + CY(i), Z = z + CZ(i);
+    if (n >= 0 && (X < 0 || X >= p.nx || Y < 0 || Y >= p.ny || Z < 0 || Z >= p.nz)) fl |= F_WRAP;
+    const int s = nbr(p, x, y, z, -CX(i), -CY(i), -CZ(i));
+    if (s < 0 || raw[s] == T_OBST) wm |= 1u << i;
+  }
+  d.flags[c] = fl;
+  d.wallmask[c] = wm;
+  const double r = den ? den[c] : 1.0;
+  d.phi[c] = (t == T_LIQ) ? 1.0 : (t == T_IFACE) ? fill[c] : 0.0;
+  d.mass[c] = (t == T_LIQ) ? r : (t == T_IFACE) ? fill[c] * r : 0.0;
+  d.cls[c] = 0;
+  d.mark[c] = 0;
+  d.conv[c] = 0;
+  d.cfin[c] = 0;
+  d.claim[c] = 0;
+  d.share[c] = 0.0;
+  typename S::T* P = (typename S::T*)d.pdf[parity];
+  typename S::T* P2 = (typename S::T*)d.pdf[parity ^ 1];
+  const bool fluid = (t == T_LIQ || t == T_IFACE);
+  const R ux = vel ? R(vel[c]) : R(0.0);
+  const R uy = vel ? R(vel[(long long)p.N + c]) : R(0.0);
+  const R uz = vel ? R(vel[2LL * p.N + c]) : R(0.0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R fe = fluid ? feq_i<Q, R>(i, R(r), ux, uy, uz) : R(0.0);
+    P[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
+    P2[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
+  }
+}
+
+// Ordered-by-warp compaction of all interface cells into a list.
+static __global__ void k_compact_full(const uint8_t* __restrict__ flags, int N, int* list,
+                               int* count) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  bool pred = (c < N) && ((flags[c] & F_TYPE) == T_IFACE);
+  int pos = warp_append(count, pred);
+  if (pred) list[pos] = c;
+}
+
+// ------------------------------------------------------------- geometry
+// K8 weights (1 - r^2/4)^4 on the 3x3x3 block: r^2 = 0, 1, 2, 3.
+template <class R>
+__device__ __forceinline__ R k8w(int n2) {
+  return n2 == 0 ? R(1.0) : n2 == 1 ? R(0.31640625) : n2 == 2 ? R(0.0625) : R(0.00390625);
+}
+
+// Geometry on 8^3 tiles that hold interface cells (tile list built by
+// k_finalize).  The tile's fill levels with a halo of 3 sit in shared memory;
+// phi~ (K8 smoothing, radius 2) is formed on the 12^3 sub-box, n^ (Parker-
+// Youngs, Eq. nm-fslbm-normal) on the 10^3 sub-box and kappa = -div(n^) on
+// the interface cells of the tile.  Obstacle and out-of-domain stencil
+// points take the stencil centre's value.  Each value uses the same
+// arithmetic and summation order as a per-cell evaluation.
+constexpr int GT = 8;                    // tile edge
+constexpr int GE = GT + 6;               // box edge with halo 3
+constexpr int GB = GE * GE * GE;         // 2744 box positions
+constexpr int GS = GT + 4;               // phi~ sub-box edge (12)
+constexpr int GN = GT + 2;               // n^ sub-box edge (10)
+constexpr int kGeoBlock = 256;
+
+template <class R>
+constexpr size_t geometry_smem() {
+  return sizeof(R) * (GB + GS * GS * GS + 3 * GN * GN * GN) + GB;
+}
+
+template <int Q, class S>
+__global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int parity) {
+  using R = typename S::Real;
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  R* sphi = (R*)g_smem;
+  R* sps = sphi + GB;
+  R* snh = sps + GS * GS * GS;
+  uint8_t* styp = (uint8_t*)(snh + 3 * GN * GN * GN);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.counts[parity ^ 1] = 0;      // next band list
+    d.counts[2] = 0;               // new-cell list
+    d.counts[3 + (parity ^ 1)] = 0;  // next tile list
+  }
+  const int ntiles = d.counts[3 + parity];
+  const int* __restrict__ tiles = d.tiles[parity];
+  const int ntx = (p.nx + GT - 1) / GT, nty = (p.ny + GT - 1) / GT;
+  R* nhat = (R*)d.nhat;
+  R* rhog = (R*)d.rhog;
+  const R wsum = R(3.6796875);
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    const int tile = tiles[tt];
+    const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int ox = tx * GT - 3, oy = ty * GT - 3, oz = tz * GT - 3;
+    __syncthreads();
+    for (int b = threadIdx.x; b < GB; b += blockDim.x) {
+      const int i = b % GE, j = (b / GE) % GE, k = b / (GE * GE);
+      const int X = wrapc(ox + i, p.nx, p.per[0]);
+      const int Y = wrapc(oy + j, p.ny, p.per[1]);
+      const int Z = wrapc(oz + k, p.nz, p.per[2]);
+      uint8_t t = 4;  // outside the domain: solid
+      R v = R(0.0);
+      if (X >= 0 && Y >= 0 && Z >= 0) {
+        const int c = X + p.nx * (Y + p.ny * Z);
+        t = d.flags[c] & F_TYPE;
+        v = R(d.phi[c]);
+      }
+      styp[b] = t;
+      sphi[b] = v;
+    }
+    __syncthreads();
+    // smoothed fill level on the 12^3 sub-box
+    for (int s = threadIdx.x; s < GS * GS * GS; s += blockDim.x) {
+      const int i = s % GS + 1, j = (s / GS) % GS + 1, k = s / (GS * GS) + 1;
+      const int b = i + GE * (j + GE * k);
+      if (styp[b] >= T_OBST) {
+        sps[s] = R(0.0);
+        continue;
+      }
+      const R pc = sphi[b];
+      R acc = R(0.0);
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int nb = b + dx + GE * (dy + GE * dz);
+            const R v = (styp[nb] >= T_OBST) ? pc : sphi[nb];
+            acc = acc + k8w<R>(dx * dx + dy * dy + dz * dz) * v;
+          }
+      sps[s] = acc / wsum;
+    }
+    __syncthreads();
+    // Parker-Youngs normal on the 10^3 sub-box
+    for (int s = threadIdx.x; s < GN * GN * GN; s += blockDim.x) {
+      const int i = s % GN + 2, j = (s / GN) % GN + 2, k = s / (GN * GN) + 2;
+      const int b = i + GE * (j + GE * k);
+      R out[3] = {R(0.0), R(0.0), R(0.0)};
+      if (styp[b] < T_OBST) {
+        auto psi = [&](int ii, int jj, int kk) { return sps[(ii - 1) + GS * ((jj - 1) + GS * (kk - 1))]; };
+        const R pc = psi(i, j, k);
+        R nn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          R acc = R(0.0);
+#pragma unroll
+          for (int pp = -1; pp <= 1; ++pp)
+#pragma unroll
+            for (int r = -1; r <= 1; ++r) {
+              const int ax = (a == 0) ? 1 : r, ay = (a == 0) ? r : (a == 1) ? 1 : pp,
+                        az = (a == 2) ? 1 : pp;
+              const int bx = (a == 0) ? -1 : ax, by = (a == 1) ? -1 : ay, bz = (a == 2) ? -1 : az;
+              const int b1 = b + ax + GE * (ay + GE * az), b2 = b + bx + GE * (by + GE * bz);
+              const R vp = (styp[b1] >= T_OBST) ? pc : psi(i + ax, j + ay, k + az);
+              const R vm = (styp[b2] >= T_OBST) ? pc : psi(i + bx, j + by, k + bz);
+              const R w = (pp == 0 && r == 0) ? R(4.0) : (pp == 0 || r == 0) ? R(2.0) : R(1.0);
+              acc = acc + w * (vp - vm);
+            }
+          nn[a] = acc;
+        }
+        const R len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[a] = (len > R(0.0)) ? nn[a] / len : R(0.0);
+      }
+      snh[s] = out[0];
+      snh[GN * GN * GN + s] = out[1];
+      snh[2 * GN * GN * GN + s] = out[2];
+    }
+    __syncthreads();
+    // curvature, gas density and Thuerey class of the tile's interface cells
+    for (int s = threadIdx.x; s < GT * GT * GT; s += blockDim.x) {
+      const int i = s % GT + 3, j = (s / GT) % GT + 3, k = s / (GT * GT) + 3;
+      const int X = ox + i, Y = oy + j, Z = oz + k;
+      if (X >= p.nx || Y >= p.ny || Z >= p.nz) continue;
+      const int b = i + GE * (j + GE * k);
+      if (styp[b] != T_IFACE) continue;
+      const int c = X + p.nx * (Y + p.ny * Z);
+      auto nh = [&](int a, int ii, int jj, int kk) {
+        return snh[a * GN * GN * GN + (ii - 2) + GN * ((jj - 2) + GN * (kk - 2))];
+      };
+      R acc = R(0.0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int ex = (a == 0), ey = (a == 1), ez = (a == 2);
+        const R vc = nh(a, i, j, k);
+        const R vp = (styp[b + ex + GE * (ey + GE * ez)] >= T_OBST) ? vc : nh(a, i + ex, j + ey, k + ez);
+        const R vm = (styp[b - ex - GE * (ey + GE * ez)] >= T_OBST) ? vc : nh(a, i - ex, j - ey, k - ez);
+        acc = acc + (vp - vm);
+      }
+      const R kappa = R(-0.5) * acc;
+      const int bb = d.bid[c];
+      const R pv = (p.bubble_model && bb >= 0) ? R(d.pV[bb]) : R(p.pv0);
+      rhog[c] = R(3.0) * (pv + R(p.sigma) * kappa);
+      nhat[3LL * c + 0] = nh(0, i, j, k);
+      nhat[3LL * c + 1] = nh(1, i, j, k);
+      nhat[3LL * c + 2] = nh(2, i, j, k);
+      bool hl = false, hg = false;
+#pragma unroll
+      for (int q = 1; q < Q; ++q) {
+        const int t = styp[b + CX(q) + GE * (CY(q) + GE * CZ(q))];
+        hl |= (t == T_LIQ);
+        hg |= (t == T_GAS);
+      }
+      d.cls[c] = (!hl && hg) ? CL_NF : (hl && !hg) ? CL_NE : CL_STD;
+    }
+    if (threadIdx.x == 0) d.tile_mark[tile] = 0;
+  }
+}
+
+// ------------------------------------------------------------ bulk sweep
+// Pull stream-collide of liquid cells (Eqs. nm-lbm-streaming, -collision)
+// with bounce-back at obstacles.  Interface and gas cells are skipped.
+// One thread per cell over the whole grid, 256 consecutive cells per block
+// (coalesced rows of the SoA slices).  Interior cells pull from constant
+// index offsets; cells next to a wall or across a periodic face take the
+// general neighbour path.
+constexpr int kBulkBlock = 256;
+
+template <int Q, class S, int COLL>
+__device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
+                                          uint8_t fl, bool general);
+
+// Persistent sweep: each warp takes 32-cell segments of the liquid segment
+// list (consecutive cells of the SoA slices, so loads and stores coalesce).
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? 4 : 2))
+    k_bulk(DPtrs d, KParams p, int parity) {
+  const int nseg = d.counts[5];
+  const int warps = (gridDim.x * kBulkBlock) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w < nseg; w += warps) {
+    const int c = d.segs[w] * 32 + lane;
+    const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_GAS;
+    const bool liq = (fl & F_TYPE) == T_LIQ;
+    // the whole warp takes the general path when one of its cells needs it
+    const bool general = __any_sync(0xffffffffu, liq && (fl & (F_NEAR_WALL | F_WRAP)));
+    if (liq) bulk_cell<Q, S, COLL>(d, p, parity, c, fl, general);
+  }
+}
+
+template <int Q, class S, int COLL>
+__device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
+                                          uint8_t fl, bool general) {
+  using R = typename S::Real;
+  using T = typename S::T;
+  const T* __restrict__ A = (const T*)d.pdf[parity];
+  T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+  const long long Np = p.Np;
+  R f[Q];
+  if (!general) {
+    const T* Ac = A + c;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = S::load(Ac[p.dofs[i]], W<Q, R>(i));
+  } else {
+    // bounce-back directions from the static wall mask; pull sources across
+    // periodic faces by branch-free index corrections
+    int x, y, z;
+    decode(p, c, x, y, z);
+    const uint32_t wm = (fl & F_NEAR_WALL) ? d.wallmask[c] : 0u;
+    const int nxy = p.nx * p.ny;
+    const int cxp = (x == 0) ? p.nx : 0, cxm = (x == p.nx - 1) ? -p.nx : 0;
+    const int cyp = (y == 0) ? nxy : 0, cym = (y == p.ny - 1) ? -nxy : 0;
+    const int czp = (z == 0) ? p.N : 0, czm = (z == p.nz - 1) ? -p.N : 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int corr = (CX(i) == 1 ? cxp : CX(i) == -1 ? cxm : 0) +
+                       (CY(i) == 1 ? cyp : CY(i) == -1 ? cym : 0) +
+                       (CZ(i) == 1 ? czp : CZ(i) == -1 ? czm : 0);
+      const long long idx = ((wm >> i) & 1u) ? (long long)OPP(i) * Np + c
+                                              : (long long)i * Np + (c - p.off[i] + corr);
+      f[i] = S::load(A[idx], W<Q, R>(((wm >> i) & 1u) ? OPP(i) : i));
+    }
+  }
+  bool bad = false;
+  collide_any<Q, S, COLL>(f, p, bad);
+  T* Bc = B + c;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Bc[(long long)i * Np] = S::store(f[i], W<Q, R>(i));
+  if (bad) d.err[0] = 1;
+}
+
+// ------------------------------------------------------- interface update
+// Pull with the free-surface BC (Eq. nm-fslbm-boundary-condition) on the
+// variant's set R (Sec. 3), mass exchange (Eq. nm-fslbm-mass-flux) with
+// Thuerey's adjustment, fill update phi = m / rho, collision, marks.
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parity) {
+  using R = typename S::Real;
+  using T = typename S::T;
+  const int* __restrict__ band = d.band[parity];
+  const int n = d.counts[parity];
+  const T* __restrict__ A = (const T*)d.pdf[parity];
+  T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+  const long long Np = p.Np;
+  const uint8_t* __restrict__ flags = d.flags;
+  const R* nhat = (const R*)d.nhat;
+  const R* rhog = (const R*)d.rhog;
+  bool bad = false;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c = band[k];
+    int x, y, z;
+    decode(p, c, x, y, z);
+    // neighbours x + c_i and their types (independent loads issued together);
+    // the pull source of direction i is the neighbour in direction ibar
+    int nid[Q];
+    int nt[Q];
+    nid[0] = c;
+    nt[0] = T_IFACE;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) nid[i] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+#pragma unroll
+    for (int i = 1; i < Q; ++i) nt[i] = ntype(flags, nid[i]);
+    R fx[Q], f[Q];
+    unsigned miss = 0u;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) fx[i] = S::load(A[(long long)i * Np + c], W<Q, R>(i));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int st = nt[OPP(i)];
+      const int src = nid[OPP(i)];
+      if (st == T_GAS) miss |= 1u << i;
+      const bool fluid = (st == T_LIQ || st == T_IFACE);
+      const T v = A[(long long)(fluid ? i : OPP(i)) * Np + (fluid ? src : c)];
+      f[i] = S::load(v, W<Q, R>(fluid ? i : OPP(i)));
+      if (st == T_GAS) f[i] = R(0.0);
+    }
+    // mass exchange with the streamed (not yet reconstructed) PDFs:
+    // a = f*_ibar(x + c_i) equals the pulled f_ibar(x)
+    const double phic = d.phi[c];
+    const int clc = d.cls[c];
+    double dm = 0.0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int ntp = nt[i];
+      if (ntp == T_GAS || ntp == T_OBST) continue;
+      const R a = f[OPP(i)];
+      const R b = fx[i];
+      if (ntp == T_LIQ) {
+        dm = dm + (double)(a - b);
+      } else {
+        const int cln = d.cls[nid[i]];
+        R v;
+        if (clc == cln) v = a - b;
+        else if (clc == CL_STD) v = (cln == CL_NF) ? a : -b;
+        else if (clc == CL_NF) v = -b;
+        else v = a;
+        dm = dm + 0.5 * (phic + d.phi[nid[i]]) * (double)v;
+      }
+    }
+    const double mn = d.mass[c] + dm;
+    // BC velocity from the cell's own post-collision PDFs
+    R rc, jx, jy, jz;
+    sums<Q, R>(fx, rc, jx, jy, jz);
+    const R ux = jx / rc - R(0.5) * R(p.g[0]);
+    const R uy = jy / rc - R(0.5) * R(p.g[1]);
+    const R uz = jz / rc - R(0.5) * R(p.g[2]);
+    // set R of the variant (Sec. 3) and reconstruction
+    const R n0 = nhat[3LL * c], n1 = nhat[3LL * c + 1], n2 = nhat[3LL * c + 2];
+    int v = p.variant;
+    if (v == 4) v = (__popc(miss) >= 3) ? 3 : p.om3_fb;
+    const R rg = rhog[c];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      bool rec = (miss >> i) & 1u;
+      const R dot = R(CX(i)) * n0 + R(CY(i)) * n1 + R(CZ(i)) * n2;
+      if (v == 1 && dot >= R(0.0)) rec = true;
+      if (v == 2 && dot > R(0.0)) rec = true;
+      if (rec) {
+        const int j = OPP(i);
+        f[i] = (feq_i<Q, R>(i, rg, ux, uy, uz) + feq_i<Q, R>(j, rg, ux, uy, uz)) - fx[j];
+      }
+    }
+    const R rho = collide_any<Q, S, COLL>(f, p, bad);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = S::store(f[i], W<Q, R>(i));
+    const double phin = mn / (double)rho;
+    d.m_next[k] = mn;
+    d.phi_next[k] = phin;
+    d.rho_band[k] = (double)rho;
+    d.mark[c] = (phin > 1.0 + p.eps) ? CV_TOL : (phin < -p.eps) ? CV_TOG : CV_NONE;
+  }
+  if (bad) d.err[0] = 1;
+}
+
+// -------------------------------------------------------------- conversion
+// Commit m, phi; conflict rule (a cell marked for gas stays interface next
+// to a cell marked for liquid); claim gas neighbours of cells turning liquid
+// and liquid neighbours of cells turning gas as new interface cells.
+template <int Q>
+__global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int parity) {
+  const int* __restrict__ band = d.band[parity];
+  const int n = d.counts[parity];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c = band[k];
+    d.mass[c] = d.m_next[k];
+    d.phi[c] = d.phi_next[k];
+    int x, y, z;
+    decode(p, c, x, y, z);
+    uint8_t cv = d.mark[c];
+    if (cv == CV_TOG) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+        if (nb >= 0 && (d.flags[nb] & F_TYPE) == T_IFACE && d.mark[nb] == CV_TOL) cv = CV_NONE;
+      }
+    }
+    d.conv[c] = cv;
+    if (cv == CV_NONE) continue;
+    const int want = (cv == CV_TOL) ? T_GAS : T_LIQ;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+      if (nb < 0 || (d.flags[nb] & F_TYPE) != want) continue;
+      unsigned* word = (unsigned*)(d.claim + (nb & ~3));
+      const unsigned bit = 1u << (8 * (nb & 3));
+      const unsigned old = atomicOr(word, bit);
+      if (!(old & bit)) d.newlist[atomicAdd(&d.counts[2], 1)] = nb;
+    }
+  }
+}
+
+// flag of a neighbour after conversion, before deferral
+__device__ __forceinline__ bool post_iface(const DPtrs& d, int nb) {
+  if (nb < 0) return false;
+  const int t = d.flags[nb] & F_TYPE;
+  if (t == T_IFACE) return d.conv[nb] == CV_NONE;
+  if (t == T_GAS || t == T_LIQ) return d.claim[nb] != 0;
+  return false;
+}
+
+// Excess-mass receivers (Eq. nm-fslbm-excess-mass): interface cells after
+// conversion in the lattice neighbourhood; none -> the conversion is deferred.
+template <int Q>
+__global__ void __launch_bounds__(kBlock) k_count(DPtrs d, KParams p, int parity) {
+  const int* __restrict__ band = d.band[parity];
+  const int n = d.counts[parity];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c = band[k];
+    const uint8_t cv = d.conv[c];
+    if (cv == CV_NONE) {
+      d.cfin[c] = CV_NONE;
+      continue;
+    }
+    int x, y, z;
+    decode(p, c, x, y, z);
+    int nrecv = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) nrecv += post_iface(d, nbr(p, x, y, z, CX(i), CY(i), CZ(i))) ? 1 : 0;
+    if (nrecv == 0) {
+      d.cfin[c] = CV_DEFER;
+    } else {
+      const double m = d.mass[c];
+      const double mex = (cv == CV_TOL) ? (m - d.rho_band[k]) : m;
+      d.share[c] = mex / (double)nrecv;
+      d.cfin[c] = cv;
+    }
+  }
+}
+
+__device__ __forceinline__ bool converted(const DPtrs& d, int nb) {
+  if (nb < 0 || (d.flags[nb] & F_TYPE) != T_IFACE) return false;
+  const uint8_t f = d.cfin[nb];
+  return f == CV_TOL || f == CV_TOG;
+}
+
+// Excess gather for all interface cells after conversion; PDFs of new
+// interface cells from gas: f* = f^eq(mean rho, mean u) over liquid and old
+// interface neighbours; new interface cells from liquid: m = rho, phi = 1.
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
+  using R = typename S::Real;
+  using T = typename S::T;
+  const int* __restrict__ band = d.band[parity];
+  const int nb_ = d.counts[parity];
+  const int nn = d.counts[2];
+  T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+  const long long Np = p.Np;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb_ + nn; k += gridDim.x * blockDim.x) {
+    const bool is_band = k < nb_;
+    const int c = is_band ? band[k] : d.newlist[k - nb_];
+    int x, y, z;
+    decode(p, c, x, y, z);
+    if (is_band) {
+      const uint8_t f = d.cfin[c];
+      if (f == CV_TOL) {
+        d.phi[c] = 1.0;
+        d.mass[c] = d.rho_band[k];
+        continue;
+      }
+      if (f == CV_TOG) {
+        d.phi[c] = 0.0;
+        d.mass[c] = 0.0;
+        continue;
+      }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+      if (converted(d, nb)) s = s + d.share[nb];
+    }
+    if (is_band) {
+      const double m = d.mass[c] + s;
+      d.mass[c] = m;
+      d.phi[c] = m / d.rho_band[k];
+      continue;
+    }
+    const int t = d.flags[c] & F_TYPE;
+    if (t == T_GAS) {
+      double sr = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+      int cnt = 0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+        if (nb < 0) continue;
+        const int nt = d.flags[nb] & F_TYPE;
+        bool use = false;
+        if (nt == T_IFACE) use = d.cfin[nb] != CV_TOG;   // stays interface or turns liquid
+        if (nt == T_LIQ) use = d.claim[nb] == 0;         // stays liquid
+        if (!use) continue;
+        R rn, un[3];
+        post_moments<Q, S>(B, Np, nb, p, rn, un);
+        sr = sr + (double)rn;
+        sx = sx + (double)un[0];
+        sy = sy + (double)un[1];
+        sz = sz + (double)un[2];
+        ++cnt;
+      }
+      double rb = 1.0, ub0 = 0.0, ub1 = 0.0, ub2 = 0.0;
+      if (cnt > 0) {
+        rb = sr / (double)cnt;
+        ub0 = sx / (double)cnt;
+        ub1 = sy / (double)cnt;
+        ub2 = sz / (double)cnt;
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        B[(long long)i * Np + c] = S::store(feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2)), W<Q, R>(i));
+      const double m = 0.0 + s;
+      d.mass[c] = m;
+      d.phi[c] = m / rb;
+    } else {  // from liquid
+      R rn, un[3];
+      post_moments<Q, S>(B, Np, c, p, rn, un);
+      const double m = (double)rn + s;
+      d.mass[c] = m;
+      d.phi[c] = m / (double)rn;
+      int best = -1;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+        if (nb < 0) continue;
+        const int nt = d.flags[nb] & F_TYPE;
+        const bool gas_after = (nt == T_GAS && d.claim[nb] == 0) || (nt == T_IFACE && d.cfin[nb] == CV_TOG);
+        const int bb = d.bid[nb];
+        if (gas_after && bb >= 0 && (best < 0 || bb < best)) best = bb;
+      }
+      d.bid[c] = best;
+    }
+  }
+}
+
+// Fixed-point bubble-volume term round((1 - phi) 2^32).
+__device__ __forceinline__ long long vol_fix(double one_minus_phi) {
+  return __double2ll_rn(one_minus_phi * 4294967296.0);
+}
+
+// Adds the geometry tile of cell c (c < 0: none) to a tile list once; every
+// lane of the warp must call it.
+__device__ __forceinline__ void mark_tile(const DPtrs& d, const KParams& p, int c, int* list,
+                                          int* count) {
+  int tile = -1;
+  if (c >= 0) {
+    int x, y, z;
+    decode(p, c, x, y, z);
+    const int ntx = (p.nx + 7) / 8, nty = (p.ny + 7) / 8;
+    tile = (x >> 3) + ntx * ((y >> 3) + nty * (z >> 3));
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, tile);
+  const bool lead = tile >= 0 && (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
+  const bool fresh = lead && atomicExch(&d.tile_mark[tile], 1) == 0;
+  const int pos = warp_append(count, fresh);
+  if (fresh) list[pos] = tile;
+}
+
+// Adds the 32-cell segment of cell c (c < 0: none) to the liquid segment list
+// once; every lane of the warp must call it.
+__device__ __forceinline__ void mark_seg(const DPtrs& d, int c) {
+  const int seg = c >= 0 ? (c >> 5) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, seg);
+  const bool lead = seg >= 0 && (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
+  const bool fresh = lead && atomicExch(&d.seg_mark[seg], 1) == 0;
+  const int pos = warp_append(&d.counts[5], fresh);
+  if (fresh) d.segs[pos] = seg;
+}
+
+// Initial liquid segment list (blocks of 256 cover whole segments).
+static __global__ void k_segs_init(DPtrs d, KParams p) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool liq = c < p.N && (d.flags[c] & F_TYPE) == T_LIQ;
+  const bool any = __any_sync(0xffffffffu, liq);
+  const bool fresh = any && (threadIdx.x & 31) == 0;
+  if (fresh) d.seg_mark[c >> 5] = 1;
+  const int pos = warp_append(&d.counts[5], fresh);
+  if (fresh) d.segs[pos] = c >> 5;
+}
+
+// Tile list of an interface list (initial state and checkpoint load).
+static __global__ void k_tiles_of_band(DPtrs d, KParams p, int parity) {
+  const int n = d.counts[parity];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int base = wid * 32; base < n; base += warps * 32) {
+    const int k = base + (threadIdx.x & 31);
+    mark_tile(d, p, k < n ? d.band[parity][k] : -1, d.tiles[parity], &d.counts[3 + parity]);
+  }
+}
+
+// Final flags, next interface list, bubble gas counts and interface sums.
+static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, int parity) {
+  const int* __restrict__ band = d.band[parity];
+  int* __restrict__ next = d.band[parity ^ 1];
+  const int nb_ = d.counts[parity];
+  const int total = nb_ + d.counts[2];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int base = wid * 32; base < total; base += warps * 32) {
+    const int k = base + lane;
+    bool keep = false, to_liq = false;
+    int c = -1, bub = -1, dgas = 0;
+    long long vfix = 0;
+    if (k < total) {
+      const bool is_band = k < nb_;
+      c = is_band ? band[k] : d.newlist[k - nb_];
+      const uint8_t fl = d.flags[c];
+      const int b = d.bid[c];
+      if (is_band) {
+        const uint8_t f = d.cfin[c];
+        if (f == CV_TOL) {
+          d.flags[c] = (fl & ~F_TYPE) | T_LIQ;
+          d.bid[c] = -1;
+          to_liq = true;
+        } else if (f == CV_TOG) {
+          d.flags[c] = (fl & ~F_TYPE) | T_GAS;
+          dgas = 1;
+        } else {
+          keep = true;
+        }
+      } else {
+        if ((fl & F_TYPE) == T_GAS) dgas = -1;
+        d.flags[c] = (fl & ~F_TYPE) | T_IFACE;
+        d.claim[c] = 0;
+        keep = true;
+      }
+      if (p.bubble_model && b >= 0) {
+        bub = b;
+        if (keep) vfix = vol_fix(1.0 - d.phi[c]);
+      }
+    }
+    if (p.bubble_model) {
+      // integer sums per bubble id present in the warp, one atomic each
+      // (integer addition: the result does not depend on the order)
+      unsigned remaining = 0xffffffffu;
+      while (remaining) {
+        const int leader = __ffs(remaining) - 1;
+        const int bb = __shfl_sync(0xffffffffu, bub, leader);
+        const bool mine = (bub == bb);
+        long long sv = mine ? vfix : 0, sg = mine ? (long long)dgas : 0;
+        for (int o = 16; o > 0; o >>= 1) {
+          sv += __shfl_xor_sync(0xffffffffu, sv, o);
+          sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        }
+        if (lane == leader && bb >= 0) {
+          if (sv) atomicAdd((unsigned long long*)&d.iface_fix[bb], (unsigned long long)sv);
+          if (sg) atomicAdd((unsigned long long*)&d.gas_cnt[bb], (unsigned long long)sg);
+        }
+        remaining &= ~__ballot_sync(0xffffffffu, mine);
+      }
+    }
+    const int pos = warp_append(&d.counts[parity ^ 1], keep);
+    if (keep) next[pos] = c;
+    mark_tile(d, p, keep ? c : -1, d.tiles[parity ^ 1], &d.counts[3 + (parity ^ 1)]);
+    mark_seg(d, to_liq ? c : -1);
+  }
+}
+
+// p^V_b = p^V_b(0) V_b(0) / V_b (Eq. nm-fslbm-pressure-volume).
+static __global__ void k_bubble(DPtrs d, KParams p) {
+  for (int b = threadIdx.x; b < d.nb; b += blockDim.x) {
+    const long long acc = d.gas_cnt[b] * 4294967296LL + d.iface_fix[b];
+    const double V = __ll2double_rn(acc) / 4294967296.0;
+    d.pV[b] = (V > 0.0) ? (p.pv0 * d.V0[b]) / V : p.pv0;
+    d.Vcur[b] = V;
+    d.iface_fix[b] = 0;
+  }
+}
+
+// ------------------------------------------------------------ observables
+// Per-block partials: [0] mass, [1] max|u|, [2] liquid volume, [3] nan,
+// [4..7] counts of gas, interface, liquid, obstacle.
+constexpr int kObsFields = 8;
+
+template <int Q, class S>
+__global__ void __launch_bounds__(kBlock) k_obs_partial(DPtrs d, KParams p, int parity,
+                                                        double* part) {
+  using R = typename S::Real;
+  const typename S::T* P = (const typename S::T*)d.pdf[parity];
+  double mass = 0.0, umax = 0.0, vol = 0.0, nan = 0.0, cnt[4] = {0, 0, 0, 0};
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < p.N; c += gridDim.x * blockDim.x) {
+    const int t = d.flags[c] & F_TYPE;
+    cnt[t] += 1.0;
+    if (t == T_LIQ || t == T_IFACE) {
+      R r, u[3];
+      post_moments<Q, S>(P, p.Np, c, p, r, u);
+      const double uu = sqrt((double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
+      if (!(uu == uu) || !(r > R(0.0))) nan = 1.0;
+      if (uu > umax) umax = uu;
+      mass += (t == T_LIQ) ? (double)r : d.mass[c];
+      vol += d.phi[c];
+      if (!(d.mass[c] == d.mass[c])) nan = 1.0;
+    }
+  }
+  __shared__ double sh[kObsFields][kBlock / 32];
+  double v[kObsFields] = {mass, umax, vol, nan, cnt[0], cnt[1], cnt[2], cnt[3]};
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < kObsFields; ++f) {
+    double a = v[f];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b = __shfl_down_sync(0xffffffffu, a, o);
+      a = (f == 1 || f == 3) ? fmax(a, b) : a + b;
+    }
+    if (lane == 0) sh[f][w] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < kObsFields) {
+    const int f = threadIdx.x;
+    double a = sh[f][0];
+    for (int i = 1; i < kBlock / 32; ++i) a = (f == 1 || f == 3) ? fmax(a, sh[f][i]) : a + sh[f][i];
+    part[blockIdx.x * kObsFields + f] = a;
+  }
+}
+
+static __global__ void k_obs_final(const double* part, int nblocks, double* out) {
+  const int f = threadIdx.x;
+  if (f >= kObsFields) return;
+  double a = part[f];
+  for (int b = 1; b < nblocks; ++b) {
+    const double v = part[b * kObsFields + f];
+    a = (f == 1 || f == 3) ? fmax(a, v) : a + v;
+  }
+  out[f] = a;
+}
+
+// PDFs of the current buffer as FP64 (zero on gas and obstacle cells).
+template <int Q, class S>
+__global__ void k_pdf_out(DPtrs d, KParams p, int parity, double* out) {
+  using R = typename S::Real;
+  const typename S::T* P = (const typename S::T*)d.pdf[parity];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const int t = d.flags[c] & F_TYPE;
+  const bool fluid = (t == T_LIQ || t == T_IFACE);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    out[(long long)i * p.N + c] = fluid ? (double)S::load(P[(long long)i * p.Np + c], W<Q, R>(i)) : 0.0;
+}
+
+}  // namespace fslbm

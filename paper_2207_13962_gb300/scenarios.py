@@ -133,16 +133,31 @@ def hydrostatic(shape, axis: int, g_abs: float, h_ref: float, flags):
 
 def _subsample_fraction(inside, shape, origin=(0.0, 0.0, 0.0), s=8):
     """Volume fraction of each cell inside a region given as a vectorised
-    predicate inside(x, y, z) of physical coordinates (s^3 sub-samples)."""
+    predicate inside(x, y, z) of physical coordinates.  Cells whose 8 corners
+    agree are taken as fully inside or outside (the regions used here are
+    unions of convex bodies much larger than a cell); the others are
+    sub-sampled with s^3 points."""
     nx, ny, nz = shape
-    off = (np.arange(s) + 0.5) / s
-    frac = np.zeros((nz, ny, nx), np.float64)
-    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    for oz in off:
-        for oy in off:
-            for ox in off:
-                frac += inside(i + ox + origin[0], j + oy + origin[1], k + oz + origin[2])
-    return frac / float(s ** 3)
+    zc, yc, xc = np.meshgrid(np.arange(nz + 1) + origin[2], np.arange(ny + 1) + origin[1],
+                             np.arange(nx + 1) + origin[0], indexing="ij")
+    corner = inside(xc, yc, zc).astype(np.int8)
+    tot = np.zeros((nz, ny, nx), np.int8)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                tot += corner[dz:dz + nz, dy:dy + ny, dx:dx + nx]
+    frac = (tot == 8).astype(np.float64)
+    mixed = np.nonzero((tot > 0) & (tot < 8))
+    if mixed[0].size:
+        k, j, i = mixed
+        off = (np.arange(s) + 0.5) / s
+        acc = np.zeros(k.size, np.float64)
+        for oz in off:
+            for oy in off:
+                for ox in off:
+                    acc += inside(i + ox + origin[0], j + oy + origin[1], k + oz + origin[2])
+        frac[mixed] = acc / float(s ** 3)
+    return frac
 
 
 # ------------------------------------------------------------------ workloads
@@ -205,17 +220,22 @@ def cylinder_dam_break(L=96, r_frac=0.3, h_frac=0.3, g=1e-5, nu=1e-3, variant="O
                     g=(0.0, 0.0, -g), steps=steps, meta=dict(L=L, R=R, H=Hh, g_abs=g, nu=nu))
 
 
-def cylinder_batch(n=64, seed=2207, lo=64, hi=160, **kw):
-    """Batch of cylindrical dam breaks with seeded cube sides U{lo..hi} and
-    radius / height fractions U(0.2, 0.4)."""
+def cylinder_batch_params(n=64, seed=2207, lo=64, hi=160):
+    """Seeded parameters of a batch of cylindrical dam breaks: cube sides
+    U{lo..hi}, radius and height fractions U(0.2, 0.4)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for _ in range(n):
         L = int(rng.integers(lo, hi + 1))
         rf = float(rng.uniform(0.2, 0.4))
         hf = float(rng.uniform(0.2, 0.4))
-        out.append(cylinder_dam_break(L=L, r_frac=rf, h_frac=hf, **kw))
+        out.append(dict(L=L, r_frac=rf, h_frac=hf))
     return out
+
+
+def cylinder_batch(n=64, seed=2207, lo=64, hi=160, **kw):
+    """Batch of cylindrical dam breaks (see cylinder_batch_params)."""
+    return [cylinder_dam_break(**prm, **kw) for prm in cylinder_batch_params(n, seed, lo, hi)]
 
 
 def taylor_bubble(nx=160, ny=160, nz=1024, D=128, bubble_d=96, bubble_len=256, z0=128,

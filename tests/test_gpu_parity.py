@@ -1,0 +1,201 @@
+"""Parity of the CUDA path (FP64 mode) with the plain CPU oracle.
+
+The FP64 kernels keep the oracle's expression order and are compiled without
+FMA contraction; the bar is identical cell flags after every step and PDFs,
+fill levels and interface masses within 1e-12 relative (absolute 1e-12 for
+values below 1).  Inputs come from the seeded generators in
+``paper_2207_13962_gb300.scenarios``; nothing here is produced by the GPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2207_13962_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["NBRC", "NBKC", "OM", "OM3"]
+TOL = 1e-12
+
+
+def _pair(sc, precision="FP64", **over):
+    from paper_2207_13962_gb300 import fslbm
+    o = Oracle(*sc.shape, **S.make_oracle_kwargs(sc, **over))
+    o.init(sc.fill, sc.flags, sc.velocity, sc.density)
+    g = fslbm.context_for(sc, precision=precision, **over)
+    return o, g
+
+
+def _close(a, b, tol=TOL):
+    return np.abs(a - b) <= tol * np.maximum(1.0, np.abs(b))
+
+
+def _compare(o, g, step, pdf=True):
+    ro = o.read()
+    rg = g.read(pdf=pdf)
+    np.testing.assert_array_equal(rg["flags"], ro["flags"], err_msg=f"flags differ at step {step}")
+    fl = ro["flags"]
+    fluid = (fl == S.LIQ) | (fl == S.IFACE)
+    iface = fl == S.IFACE
+    bad = ~_close(rg["fill"], ro["fill"])
+    assert not bad.any(), f"fill differs at step {step}: max {np.abs(rg['fill'] - ro['fill']).max()}"
+    bad = ~_close(rg["mass"][iface], ro["mass"][iface])
+    assert not bad.any(), f"mass differs at step {step}"
+    if pdf:
+        d = ~_close(rg["pdf"][:, fluid], ro["pdf"][:, fluid])
+        assert not d.any(), f"pdf differs at step {step}: max {np.abs(rg['pdf'][:, fluid] - ro['pdf'][:, fluid]).max()}"
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_gravity_wave_1000_steps(variant, gpu_lib):
+    """32 x 64 x 1, D3Q19 TRT FP64, nu = 0.01, g = 1e-5, 1000 steps."""
+    sc = S.gravity_wave(variant=variant)
+    o, g = _pair(sc)
+    for s in range(1, 1001):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, s, pdf=(s % 50 == 0))
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_stress_ragged_domain(q, variant, gpu_lib):
+    """Ragged 37 x 21 x 11 domain with obstacles, random velocities, surface
+    tension and gravity: conversions in both directions every few steps."""
+    sc = S.random_interface(shape=(37, 21, 11), seed=7, q=q, variant=variant)
+    o, g = _pair(sc)
+    for s in range(1, 151):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, s, pdf=(s % 10 == 0))
+
+
+@pytest.mark.parametrize("collision", ["SRT", "TRT"])
+def test_stress_collision_and_fallback(collision, gpu_lib):
+    sc = S.random_interface(shape=(24, 18, 9), seed=11, q=19, variant="OM3", periodic=(True, True, False))
+    o, g = _pair(sc, collision=collision, om3_fallback="NBRC")
+    for s in range(1, 101):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, s, pdf=(s % 10 == 0))
+
+
+def test_bubble_model_parity(gpu_lib):
+    sc = S.taylor_bubble(nx=24, ny=24, nz=64, D=20, bubble_d=12, bubble_len=20, z0=12,
+                         z_ref=40.0, g=2e-5, sigma=2e-3, nu=0.02)
+    o, g = _pair(sc)
+    for s in range(1, 121):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, s, pdf=(s % 20 == 0))
+    Vo, Po, _ = o.bubbles()
+    Vg, Pg = g.bubbles()
+    assert len(Vo) == len(Vg) == 1
+    np.testing.assert_allclose(Vg, Vo, rtol=1e-13)
+    np.testing.assert_allclose(Pg, Po, rtol=1e-13)
+
+
+def test_dam_break_full_size_first_steps(gpu_lib):
+    """256 x 128 x 64 dam break (the benchmark workload) in FP64: all fields
+    after 3 steps; then 40 more GPU steps against invariants."""
+    sc = S.dam_break(variant="OM")
+    o, g = _pair(sc)
+    for s in range(1, 4):
+        o.step(1)
+        g.step(1)
+    _compare(o, g, 3)
+    M0 = o.total_mass()
+    g.step(40)
+    obs = g.observables()
+    assert obs["status"] == 0
+    assert abs(obs["total_mass"] - M0) / M0 < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(1, 9, 1), (5, 3, 2), (33, 1, 7)])
+def test_degenerate_domains(shape, gpu_lib):
+    """Thin and one-cell-wide domains (periodic wrap onto the cell itself)."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(5)
+    j = np.arange(ny)
+    phi = np.clip(ny / 2.0 + 0.3 - j, 0, 1)[None, :, None] * np.ones((nz, ny, nx))
+    fill, flags = S.classify(phi, None, (True, False, True), 19)
+    vel = np.where(np.repeat((flags == S.LIQ) | (flags == S.IFACE), 3), rng.uniform(-0.01, 0.01, 3 * fill.size), 0.0)
+    sc = S.Scenario("thin", shape, (True, False, True), fill, flags, vel, None, omega=1.2,
+                    g=(0.0, -1e-4, 0.0), sigma=1e-3)
+    o, g = _pair(sc)
+    for s in range(1, 41):
+        o.step(1)
+        g.step(1)
+        _compare(o, g, s)
+
+
+def test_all_liquid_and_all_gas(gpu_lib):
+    """No interface cells at all: the band is empty."""
+    from paper_2207_13962_gb300 import fslbm
+    shape = (16, 16, 4)
+    N = 16 * 16 * 4
+    rng = np.random.default_rng(3)
+    vel = rng.uniform(-0.02, 0.02, 3 * N)
+    sc = S.Scenario("liquid", shape, (True, True, True), np.ones(N), np.full(N, S.LIQ, np.uint8),
+                    vel, None, omega=1.5, g=(1e-5, 0, 0))
+    o, g = _pair(sc)
+    o.step(25)
+    g.step(25)
+    _compare(o, g, 25)
+    assert g.interface_count() == 0
+    gas = fslbm.Context(shape, periodic=(True, True, True), precision="FP64")
+    gas.init(np.zeros(N), np.zeros(N, np.uint8))
+    gas.step(5)
+    r = gas.read()
+    assert np.all(r["flags"] == S.GAS)
+
+
+def test_invalid_inputs(gpu_lib):
+    from paper_2207_13962_gb300 import fslbm
+    shape = (8, 8, 2)
+    N = 128
+    ctx = fslbm.Context(shape, precision="FP64")
+    with pytest.raises(fslbm.FslbmError) as e:
+        ctx.step(1)
+    assert e.value.status == fslbm.ESTATE
+    flags = np.full(N, S.LIQ, np.uint8)
+    flags[5] = S.GAS  # liquid next to gas: interface layer not closed
+    with pytest.raises(fslbm.FslbmError) as e:
+        ctx.init(np.ones(N), flags)
+    assert e.value.status == fslbm.EINVAL
+    flags[5] = 7
+    with pytest.raises(fslbm.FslbmError) as e:
+        ctx.init(np.ones(N), flags)
+    assert e.value.status == fslbm.EINVAL
+    with pytest.raises(fslbm.FslbmError):
+        fslbm.Context((0, 4, 4))
+
+
+def test_checkpoint_roundtrip_is_bitwise(gpu_lib):
+    sc = S.random_interface(shape=(20, 18, 6), seed=2)
+    from paper_2207_13962_gb300 import fslbm
+    a = fslbm.context_for(sc, precision="FP64")
+    b = fslbm.context_for(sc, precision="FP64")
+    a.step(60)
+    b.step(30)
+    buf = b.save()
+    c = fslbm.context_for(sc, precision="FP64")
+    c.load(buf)
+    c.step(30)
+    ra, rc = a.read(), c.read()
+    for k in ("pdf", "fill", "flags"):
+        np.testing.assert_array_equal(ra[k], rc[k])
+
+
+def test_timing_mode_matches_graph_mode(gpu_lib):
+    sc = S.random_interface(shape=(20, 18, 6), seed=4)
+    from paper_2207_13962_gb300 import fslbm
+    a = fslbm.context_for(sc, precision="FP64")
+    b = fslbm.context_for(sc, precision="FP64")
+    b.set_timing(True)
+    a.step(20)
+    b.step(20)
+    ra, rb = a.read(), b.read()
+    np.testing.assert_array_equal(ra["pdf"], rb["pdf"])
+    times, launches = b.stage_times()
+    assert launches == 20 * 7 and times["bulk"] > 0
