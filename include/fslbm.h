@@ -177,6 +177,27 @@ fslbm_status fslbm_interface_count(fslbm_ctx* ctx, int64_t* n);
 fslbm_status fslbm_work_counts(fslbm_ctx* ctx, int64_t* interface_cells,
                                int64_t* liquid_segments, int64_t* geometry_tiles);
 
+/* Whole-domain observables of a state held in caller-provided device memory,
+ * for callers that may not allocate device memory (their device memory is
+ * owned by another allocator, or an allocation would stall a latency-critical
+ * loop).  The paper has no counterpart: this is a service of the library.
+ * Same results as fslbm_observables on the same state.
+ *   domain: sizes (periodic flags unused); q: 19 or 27; g[3]: gravity (host).
+ *   pdf: device, q*N FP64 post-collision PDFs, direction-major (stride N).
+ *   flags, fill, mass: device, N entries each (flags 0..3, higher bits ignored).
+ *   out: host; stream: cudaStream_t or NULL.  Synchronizes the stream.
+ * Allocates nothing: the block partials live in a fixed 66 KB device array
+ * of the library (held by every GPU that loads it until the process exits).
+ * The first call on a device looks up that array's device address; make it
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.  FSLBM_EINVAL for q not 19/27, empty domains or
+ * more than 2^31 - 1 cells; FSLBM_ECUDA if a CUDA call fails. */
+fslbm_status fslbm_observables_noalloc(const fslbm_domain* domain, int q, const double* g,
+                                       const double* pdf, const uint8_t* flags,
+                                       const double* fill, const double* mass,
+                                       fslbm_obs* out, void* stream);
+
 void fslbm_destroy(fslbm_ctx* ctx);
 const char* fslbm_last_error(const fslbm_ctx* ctx);
 const char* fslbm_version(void);

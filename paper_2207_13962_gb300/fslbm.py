@@ -51,7 +51,7 @@ _lock = threading.Lock()
 SYMBOLS = ["fslbm_params_default", "fslbm_create", "fslbm_init", "fslbm_step", "fslbm_sync",
            "fslbm_observables", "fslbm_read_fields", "fslbm_bubbles", "fslbm_set_timing",
            "fslbm_stage_times", "fslbm_save", "fslbm_load", "fslbm_interface_count", "fslbm_work_counts",
-           "fslbm_destroy", "fslbm_last_error", "fslbm_version"]
+           "fslbm_observables_noalloc", "fslbm_destroy", "fslbm_last_error", "fslbm_version"]
 
 
 def load(build_if_missing: bool = True):
@@ -96,6 +96,9 @@ def load(build_if_missing: bool = True):
         lib.fslbm_interface_count.restype = i
         lib.fslbm_work_counts.argtypes = [p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         lib.fslbm_work_counts.restype = i
+        lib.fslbm_observables_noalloc.argtypes = [C.POINTER(fslbm_domain), i, p, p, p, p, p,
+                                                  C.POINTER(fslbm_obs), p]
+        lib.fslbm_observables_noalloc.restype = i
         lib.fslbm_destroy.argtypes = [p]
         lib.fslbm_destroy.restype = None
         lib.fslbm_last_error.argtypes = [p]
