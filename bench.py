@@ -60,6 +60,11 @@ def max_over_ranks(value: float, ws: int) -> float:
     return float(t.item())
 
 
+def whole_job_mlups(cells_per_rank: int, ws: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: cell updates of all ranks over the slowest rank's time."""
+    return cells_per_rank * ws * steps / (ms * 1e-3) / 1e6
+
+
 def barrier(ws: int):
     if ws > 1:
         import torch.distributed as dist
@@ -249,7 +254,7 @@ def bench_ours(args, ws, rank, local):
     st = ctx.sync()
     obs1 = ctx.observables()
     ms = max_over_ranks(ms_local, ws)
-    value = N * ws * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(N, ws, args.steps, ms)
 
     # ---- per-stage CUDA-event timing (kernels launched one by one on the
     # context's stream) for the roofline of the dominant kernel
