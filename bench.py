@@ -145,6 +145,10 @@ def make_workload(name: str, variant: str):
         sc = S.taylor_bubble(variant=variant)
         desc = ("rising Taylor bubble 160x160x1024, tube D=128, bubble 96x256, D3Q19 TRT, "
                 "g=1e-6, sigma=1e-4, nu=5e-3, bubble model")
+    elif name == "taylor_bubble_256":
+        sc = S.taylor_bubble(nz=256, bubble_len=96, z0=64, z_ref=128.0, variant=variant)
+        desc = ("rising Taylor bubble, short tube 160x160x256 (profiling case), bubble 96x96, D3Q19 TRT, "
+                "g=1e-6, sigma=1e-4, nu=5e-3, bubble model")
     elif name == "dam_break":
         sc = S.dam_break(variant=variant)
         desc = "rectangular dam break 256x128x64, column 64^3, D3Q19 TRT, g=1e-5, nu=1e-3, no-slip"
@@ -159,30 +163,7 @@ def make_workload(name: str, variant: str):
 def oracle_sample(sc, name: str, zlo: int, zhi: int):
     """A z-slab of the workload's initial state (walls at the cut faces)."""
     from paper_2207_13962_gb300 import scenarios as S
-    nx, ny, nz = sc.shape
-    zlo, zhi = max(0, zlo), min(nz, zhi)
-    sl = slice(zlo * nx * ny, zhi * nx * ny)
-    fill = sc.fill[sl].copy()
-    flags = sc.flags[sl].copy()
-    den = None if sc.density is None else sc.density[sl].copy()
-    vel = None
-    if sc.velocity is not None:
-        N = nx * ny * nz
-        vel = np.concatenate([sc.velocity[a * N:(a + 1) * N][sl] for a in range(3)])
-    shape = (nx, ny, zhi - zlo)
-    per = (sc.periodic[0], sc.periodic[1], False)
-    # the cut faces become walls: restore closure in case a cut exposed a liquid-gas contact
-    f3 = flags.reshape(shape[2], ny, nx)
-    p3 = fill.reshape(shape[2], ny, nx)
-    gas = f3 == S.GAS
-    for dx, dy, dz in S.neighbour_offsets(sc.q):
-        sh = S._shift(S._shift(S._shift(gas, dz, 0, per[2], False), dy, 1, per[1], False), dx, 2, per[0], False)
-        fix = sh & (f3 == S.LIQ)
-        f3[fix] = S.IFACE
-        p3[fix] = 1.0
-    return S.Scenario(f"{name}[z={zlo}:{zhi}]", shape, per, fill, flags, vel, den, q=sc.q,
-                      collision=sc.collision, variant=sc.variant, omega=sc.omega, g=sc.g,
-                      sigma=sc.sigma, bubble_model=sc.bubble_model)
+    return S.z_slab(sc, zlo, zhi)
 
 
 def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50):
@@ -191,6 +172,8 @@ def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50):
     from paper_2207_13962_gb300 import scenarios as S
     if name == "taylor_bubble":
         smp = oracle_sample(sc, name, 352, 416)
+    elif name == "taylor_bubble_256":
+        smp = oracle_sample(sc, name, 128, 160)
     elif name == "box512":
         smp = oracle_sample(sc, name, 448, 512)
     else:
@@ -267,8 +250,8 @@ def bench_ours(args, ws, rank, local):
     n_liq = 0.5 * (obs1["n_liquid"] + obs2["n_liquid"])
     nseg = ctx.work_counts()["liquid_segments"]
     # algorithmic bytes of one bulk launch: read + write q PDFs per liquid
-    # cell, one flag byte per cell of the swept 32-cell segments
-    alg_bytes = n_liq * 2 * Q * S_BYTES[prec] + nseg * 32
+    # cell, one flag byte per cell of the swept 8-cell groups
+    alg_bytes = n_liq * 2 * Q * S_BYTES[prec] + nseg * 8
     achieved = alg_bytes / (bulk_ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -411,7 +394,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "dam_break", "box512"])
+    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "taylor_bubble_256", "dam_break", "box512"])
     ap.add_argument("--precision", default="FP32", choices=list(S_BYTES))
     ap.add_argument("--variant", default="OM", choices=["NBRC", "NBKC", "OM", "OM3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -67,9 +67,12 @@ typedef enum {
   FSLBM_OM3 = 4   /* Eq. fsbcv-om3: OM if |G-| >= 3, else the fallback    */
 } fslbm_bc_variant;
 
-/* Storage of the PDFs; arithmetic is FP64 for FSLBM_FP64 and FP32 otherwise.
- * Fill level, mass, excess mass and bubble volumes are always FP64.
- * FP16S / BF16S store the shifted deviation f_i - w_i. */
+/* Storage of the PDFs.  FSLBM_FP64 stores f_i and computes in FP64 with the
+ * expressions of the plain CPU oracle.  FSLBM_FP32, FP16S and BF16S store the
+ * deviation d_i = f_i - w_i from the rest state (FP16 as d_i * 2^15) and
+ * compute in FP32 on deviations, so that rounding is relative to |d| ~ 1e-3
+ * rather than to |f|.  Fill level, mass, excess mass, the mass flux between
+ * cells and bubble volumes are always FP64. */
 typedef enum {
   FSLBM_FP64 = 0,
   FSLBM_FP32 = 1,
@@ -172,7 +175,7 @@ fslbm_status fslbm_load(fslbm_ctx* ctx, const void* buf, size_t size);
 fslbm_status fslbm_interface_count(fslbm_ctx* ctx, int64_t* n);
 
 /* Sizes of the work lists of the next step (synchronizes; any pointer may be
- * NULL): interface cells, 32-cell segments swept by the bulk kernel (those
+ * NULL): interface cells, 8-cell groups swept by the bulk kernel (those
  * that hold or held liquid) and 8^3 geometry tiles holding interface cells. */
 fslbm_status fslbm_work_counts(fslbm_ctx* ctx, int64_t* interface_cells,
                                int64_t* liquid_segments, int64_t* geometry_tiles);

@@ -46,6 +46,13 @@ namespace {
 
 const char* kVersion = "fslbm-gb300 1.0";
 
+#ifndef FSLBM_BAND_PRIO
+#define FSLBM_BAND_PRIO 1
+#endif
+#ifndef FSLBM_BULK_RESERVE
+#define FSLBM_BULK_RESERVE 0
+#endif
+
 fslbm_status fail(fslbm_ctx* c, fslbm_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
@@ -85,6 +92,42 @@ void destroy_graphs(fslbm_ctx* c) {
     }
 }
 
+// The interface-band kernels form a chain of short, latency-bound launches
+// that runs beside the bulk sweep on a forked stream; giving their graph
+// nodes the device's highest priority lets the block scheduler place their
+// blocks first whenever an SM has room, so the chain finishes under the
+// bandwidth-bound sweep instead of after it.
+cudaError_t prioritise_band(fslbm_ctx* c, cudaGraph_t g) {
+#if FSLBM_BAND_PRIO
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return e;
+  size_t n = 0;
+  e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess || n == 0) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  e = cudaGraphGetNodes(g, nodes.data(), &n);
+  for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[i], &t);
+    if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+    if (e != cudaSuccess) break;
+    if (kp.func == c->ops.bulk_fn[0] || kp.func == c->ops.bulk_fn[1]) continue;
+    cudaLaunchAttributeValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.priority = greatest;
+    e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
+  }
+  return e;
+#else
+  (void)c;
+  (void)g;
+  return cudaSuccess;
+#endif
+}
+
 cudaError_t build_graphs(fslbm_ctx* c) {
   destroy_graphs(c);
   for (int par = 0; par < 2; ++par) {
@@ -94,7 +137,8 @@ cudaError_t build_graphs(fslbm_ctx* c) {
     c->ops.step(c->d, c->kp, par, c->band_grid, c->bulk_grid, c->cap_stream, nullptr, &c->fork);
     e = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&c->graph[par], g, 0);
+    e = prioritise_band(c, g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[par], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return e;
   }
@@ -246,7 +290,9 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
   c->band_grid = sms * 2;
-  c->bulk_grid = sms * (params->precision == FSLBM_FP64 ? 2 : 4);
+  // the persistent bulk sweep leaves FSLBM_BULK_RESERVE block slots per SM to
+  // the interface-band kernels that run beside it
+  c->bulk_grid = sms * ((params->precision == FSLBM_FP64 ? 2 : kBulkMinBlocks32) - FSLBM_BULK_RESERVE);
 
   DPtrs& d = c->d;
   std::memset(&d, 0, sizeof(d));
@@ -276,7 +322,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   ALLOC(d.tiles[0], ntiles * sizeof(int));
   ALLOC(d.tiles[1], ntiles * sizeof(int));
   ALLOC(d.tile_mark, ntiles * sizeof(int));
-  const long long nseg = (N + 31) / 32;
+  const long long nseg = (N + kSegCells - 1) / kSegCells;
   ALLOC(d.segs, nseg * sizeof(int));
   ALLOC(d.seg_mark, nseg * sizeof(int));
   ALLOC(d.newlist, N * sizeof(int));
@@ -434,7 +480,7 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
     k_tiles_of_band<<<c->band_grid, kBlock, 0, st>>>(d, c->kp, 0);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.seg_mark, 0, (size_t)((N + 31) / 32) * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.seg_mark, 0, (size_t)((N + kSegCells - 1) / kSegCells) * sizeof(int), st);
   if (e == cudaSuccess) {
     k_segs_init<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, st>>>(d, c->kp);
     e = cudaGetLastError();
@@ -715,7 +761,7 @@ fslbm_status fslbm_load(fslbm_ctx* c, const void* buf, size_t size) {
     k_tiles_of_band<<<c->band_grid, kBlock, 0, c->stream>>>(c->d, c->kp, 0);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d.seg_mark, 0, (size_t)((N + 31) / 32) * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d.seg_mark, 0, (size_t)((N + kSegCells - 1) / kSegCells) * sizeof(int), c->stream);
   if (e == cudaSuccess) {
     k_segs_init<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(c->d, c->kp);
     e = cudaGetLastError();

@@ -76,12 +76,23 @@ __host__ __device__ constexpr R W(int i) {
 }
 
 // -------------------------------------------------------------- storage
-// Real: arithmetic type; T: stored type; load/store convert with the
-// shift f - w_i for the 16-bit formats.
+// T: stored type; Real: arithmetic type.
+//
+// FP64 stores f and computes in FP64 with the plain CPU oracle's expressions
+// (bitwise parity).  The other formats store the deviation d = f - w_i from
+// the rest state and compute in FP32 on deviations: with |d| ~ 1e-3 instead
+// of |f| ~ 0.1, the rounding of every stored value and of every collision is
+// ~100x smaller in absolute terms, which is what keeps the liquid mass (a sum
+// of stored PDFs) from drifting.  FP16 stores d * 2^15 (|d| <= 1 stays below
+// the FP16 maximum 65504, and deviations down to ~4e-9 stay normal numbers);
+// BF16 has FP32's exponent range and stores d unscaled.
+//   loadd / stored: stored value <-> deviation (FP32 formats only)
+//   load / store:   stored value <-> absolute PDF f
 struct StoreF64 {
   using T = double;
   using Real = double;
   static constexpr int code = 0;
+  static constexpr bool kDev = false;
   __device__ static __forceinline__ Real load(T v, Real) { return v; }
   __device__ static __forceinline__ T store(Real f, Real) { return f; }
 };
@@ -89,22 +100,31 @@ struct StoreF32 {
   using T = float;
   using Real = float;
   static constexpr int code = 1;
-  __device__ static __forceinline__ Real load(T v, Real) { return v; }
-  __device__ static __forceinline__ T store(Real f, Real) { return f; }
+  static constexpr bool kDev = true;
+  __device__ static __forceinline__ float loadd(T v) { return v; }
+  __device__ static __forceinline__ T stored(float d) { return d; }
+  __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
 };
 struct StoreF16S {
   using T = __half;
   using Real = float;
   static constexpr int code = 2;
-  __device__ static __forceinline__ Real load(T v, Real w) { return __half2float(v) + w; }
-  __device__ static __forceinline__ T store(Real f, Real w) { return __float2half_rn(f - w); }
+  static constexpr bool kDev = true;
+  __device__ static __forceinline__ float loadd(T v) { return __half2float(v) * 0x1p-15f; }
+  __device__ static __forceinline__ T stored(float d) { return __float2half_rn(d * 0x1p15f); }
+  __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
 };
 struct StoreBF16S {
   using T = __nv_bfloat16;
   using Real = float;
   static constexpr int code = 3;
-  __device__ static __forceinline__ Real load(T v, Real w) { return __bfloat162float(v) + w; }
-  __device__ static __forceinline__ T store(Real f, Real w) { return __float2bfloat16_rn(f - w); }
+  static constexpr bool kDev = true;
+  __device__ static __forceinline__ float loadd(T v) { return __bfloat162float(v); }
+  __device__ static __forceinline__ T stored(float d) { return __float2bfloat16_rn(d); }
+  __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
 };
 
 // ------------------------------------------------- division by invariants
@@ -124,6 +144,24 @@ inline FastDiv make_fastdiv(unsigned d) {
   f.m = (unsigned)((((1ull << f.l) - d) << 32) / d + 1ull);
   return f;
 }
+
+// Resident blocks of 256 threads per SM that the bulk sweep is compiled for
+// (FP32 arithmetic; the FP64 engine uses 2); its persistent grid is this
+// many blocks per SM.
+#ifndef FSLBM_BULK_MINB
+#define FSLBM_BULK_MINB 4
+#endif
+constexpr int kBulkMinBlocks32 = FSLBM_BULK_MINB;
+
+// Granularity of the bulk sweep's work list: groups of kSegCells consecutive
+// cells that hold liquid (8 = one 32-byte sector of an FP32 PDF slice).  A
+// warp takes 32 / kSegCells groups, so lanes are spent on liquid cells rather
+// than on the gas, obstacle and interface cells around them.
+#ifndef FSLBM_SEG_CELLS
+#define FSLBM_SEG_CELLS 8
+#endif
+constexpr int kSegCells = FSLBM_SEG_CELLS;
+static_assert(kSegCells == 8 || kSegCells == 16 || kSegCells == 32, "segment size");
 
 // ----------------------------------------------------------- parameters
 struct KParams {

@@ -81,6 +81,8 @@ struct Engine {
     o.pdf_out = &pdf_out;
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::Real);
+    o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
+    o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
     return o;
   }
 };

@@ -34,6 +34,8 @@ struct Ops {
   void (*pdf_out)(const DPtrs&, const KParams&, int parity, double* out, cudaStream_t);
   size_t elem_size;
   size_t real_size;
+  const void* bulk_fn[2];  // the bulk sweep kernels (SRT, TRT): graph nodes of
+                           // every other kernel get the higher priority
 };
 
 // Defined in fslbm_f64.cu, fslbm_f32.cu, fslbm_f16.cu.

@@ -160,21 +160,32 @@ __device__ __forceinline__ R collide(R* f, const KParams& p, bool& unstable) {
   return rho;
 }
 
-// Collision for the FP32 path: the same TRT/SRT with Guo forcing, evaluated
-// per direction pair (i, ibar) from the symmetric and antisymmetric parts of
-// f^eq (w rho (1 + 4.5 (c.u)^2 - 1.5 u.u) and 3 w rho c.u) and of the source.
-// SRT is the case omega- = omega+.  Fewer operations and live registers than
-// the per-direction form that the FP64 path keeps for bitwise parity.
+// Equilibrium deviation f^eq_i - w_i = w_i (drho + rho (3 c.u + 4.5 (c.u)^2
+// - 1.5 u.u)) with drho = rho - 1 (Eq. nm-lbm-equilibrium).
+template <int Q, class R>
+__device__ __forceinline__ R feq_dev(int i, R drho, R rho, R ux, R uy, R uz) {
+  const R cu = R(CX(i)) * ux + R(CY(i)) * uy + R(CZ(i)) * uz;
+  const R usq = ux * ux + uy * uy + uz * uz;
+  return W<Q, R>(i) * (drho + rho * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+}
+
+// Collision of the FP32 engines on deviations d_i = f_i - w_i (the same
+// TRT/SRT with Guo forcing as collide()).  Evaluated per direction pair
+// (i, ibar) from the symmetric and antisymmetric parts of f^eq - w
+// (w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)) and 3 w rho c.u) and of the
+// source; SRT is the case omega- = omega+.  Every intermediate is of the
+// size of a deviation, so its rounding is too.  Returns drho.
 template <int Q, int COLL>
-__device__ __forceinline__ float collide_fast(float* f, const KParams& p, bool& unstable) {
-  float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+__device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& unstable) {
+  float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    rho += f[i];
-    if (CX(i) != 0) jx += float(CX(i)) * f[i];
-    if (CY(i) != 0) jy += float(CY(i)) * f[i];
-    if (CZ(i) != 0) jz += float(CZ(i)) * f[i];
+    dr += d[i];
+    if (CX(i) != 0) jx += float(CX(i)) * d[i];
+    if (CY(i) != 0) jy += float(CY(i)) * d[i];
+    if (CZ(i) != 0) jz += float(CZ(i)) * d[i];
   }
+  const float rho = 1.0f + dr;
   const float gx = float(p.g[0]), gy = float(p.g[1]), gz = float(p.g[2]);
   const float inv = __frcp_rn(rho);
   const float ux = jx * inv + 0.5f * gx, uy = jy * inv + 0.5f * gy, uz = jz * inv + 0.5f * gz;
@@ -183,12 +194,11 @@ __device__ __forceinline__ float collide_fast(float* f, const KParams& p, bool& 
   if (!(usq < 1.0f / 3.0f) || !(rho > 0.f)) unstable = true;
   const float omp = float(p.omega), prp = float(p.pref_p);
   const float omm = COLL == 0 ? omp : float(p.om_m), prm = COLL == 0 ? prp : float(p.pref_m);
-  const float base = 1.0f - 1.5f * usq;
+  const float base = dr - 1.5f * rho * usq;
   const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
   {
     const float w = W<Q, float>(0);
-    const float es = w * rho * base;
-    f[0] = f[0] - omp * (f[0] - es) - prp * w * uF3;
+    d[0] = d[0] - omp * (d[0] - w * base) - prp * w * uF3;
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -196,45 +206,75 @@ __device__ __forceinline__ float collide_fast(float* f, const KParams& p, bool& 
     const float w = W<Q, float>(i);
     const float cu = float(CX(i)) * ux + float(CY(i)) * uy + float(CZ(i)) * uz;
     const float cF = float(CX(i)) * Fx + float(CY(i)) * Fy + float(CZ(i)) * Fz;
-    const float es = w * rho * (base + 4.5f * cu * cu);
+    const float es = w * (base + 4.5f * rho * cu * cu);
     const float ea = 3.0f * w * rho * cu;
     const float ss = w * (9.0f * cu * cF - uF3);
     const float sa = 3.0f * w * cF;
-    const float fp = 0.5f * (f[i] + f[j]);
-    const float fm = 0.5f * (f[i] - f[j]);
+    const float fp = 0.5f * (d[i] + d[j]);
+    const float fm = 0.5f * (d[i] - d[j]);
     const float A = omp * (fp - es) - prp * ss;
     const float B = omm * (fm - ea) - prm * sa;
-    const float fi = f[i] - A - B;
-    const float fj = f[j] - A + B;
-    f[i] = fi;
-    f[j] = fj;
+    const float di = d[i] - A - B;
+    const float dj = d[j] - A + B;
+    d[i] = di;
+    d[j] = dj;
   }
-  return rho;
+  return dr;
 }
 
+// Collision in the engine's working representation (absolute f in FP64,
+// deviations otherwise); returns rho.
 template <int Q, class S, int COLL>
-__device__ __forceinline__ typename S::Real collide_any(typename S::Real* f, const KParams& p,
-                                                        bool& unstable) {
-  if constexpr (S::code == 0)
+__device__ __forceinline__ double collide_any(typename S::Real* f, const KParams& p,
+                                              bool& unstable) {
+  if constexpr (!S::kDev)
     return collide<Q, double, COLL>(f, p, unstable);
   else
-    return collide_fast<Q, COLL>(f, p, unstable);
+    return 1.0 + (double)collide_dev<Q, COLL>(f, p, unstable);
+}
+
+// PDF i of cell c in the working representation.
+template <class S, int Q>
+__device__ __forceinline__ typename S::Real load_w(typename S::T v, int i) {
+  if constexpr (S::kDev)
+    return S::loadd(v);
+  else
+    return S::load(v, W<Q, typename S::Real>(i));
+}
+template <class S, int Q>
+__device__ __forceinline__ typename S::T store_w(typename S::Real v, int i) {
+  if constexpr (S::kDev)
+    return S::stored(v);
+  else
+    return S::store(v, W<Q, typename S::Real>(i));
 }
 
 // rho and u of a cell from its post-collision PDFs: rho u = sum c f* - F/2.
+// With deviations, rho = 1 + sum d is summed in FP64 from the stored values,
+// so that it equals the cell's mass as the PDFs hold it.
 template <int Q, class S>
 __device__ __forceinline__ void post_moments(const typename S::T* P, long long Np, int c,
-                                             const KParams& p, typename S::Real& rho,
+                                             const KParams& p, double& rho,
                                              typename S::Real u[3]) {
   using R = typename S::Real;
   R f[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = S::load(P[(long long)i * Np + c], W<Q, R>(i));
-  R jx, jy, jz;
-  sums<Q, R>(f, rho, jx, jy, jz);
-  u[0] = jx / rho - R(0.5) * R(p.g[0]);
-  u[1] = jy / rho - R(0.5) * R(p.g[1]);
-  u[2] = jz / rho - R(0.5) * R(p.g[2]);
+  for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(P[(long long)i * Np + c], i);
+  R r, jx, jy, jz;
+  sums<Q, R>(f, r, jx, jy, jz);
+  R rr = r;
+  if constexpr (S::kDev) {
+    double sd = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sd += (double)f[i];
+    rho = 1.0 + sd;
+    rr = R(rho);
+  } else {
+    rho = r;
+  }
+  u[0] = jx / rr - R(0.5) * R(p.g[0]);
+  u[1] = jy / rr - R(0.5) * R(p.g[1]);
+  u[2] = jz / rr - R(0.5) * R(p.g[2]);
 }
 
 // ------------------------------------------------------------------ init
@@ -294,14 +334,27 @@ __global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __re
   typename S::T* P = (typename S::T*)d.pdf[parity];
   typename S::T* P2 = (typename S::T*)d.pdf[parity ^ 1];
   const bool fluid = (t == T_LIQ || t == T_IFACE);
-  const R ux = vel ? R(vel[c]) : R(0.0);
-  const R uy = vel ? R(vel[(long long)p.N + c]) : R(0.0);
-  const R uz = vel ? R(vel[2LL * p.N + c]) : R(0.0);
+  if constexpr (S::kDev) {
+    // deviation f^eq - w formed in FP64, rounded once to the stored format
+    const double ux = vel ? vel[c] : 0.0;
+    const double uy = vel ? vel[(long long)p.N + c] : 0.0;
+    const double uz = vel ? vel[2LL * p.N + c] : 0.0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    R fe = fluid ? feq_i<Q, R>(i, R(r), ux, uy, uz) : R(0.0);
-    P[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
-    P2[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
+    for (int i = 0; i < Q; ++i) {
+      const double de = fluid ? feq_dev<Q, double>(i, r - 1.0, r, ux, uy, uz) : -W<Q, double>(i);
+      P[(long long)i * p.Np + c] = S::stored(float(de));
+      P2[(long long)i * p.Np + c] = S::stored(float(de));
+    }
+  } else {
+    const R ux = vel ? R(vel[c]) : R(0.0);
+    const R uy = vel ? R(vel[(long long)p.N + c]) : R(0.0);
+    const R uz = vel ? R(vel[2LL * p.N + c]) : R(0.0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R fe = fluid ? feq_i<Q, R>(i, R(r), ux, uy, uz) : R(0.0);
+      P[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
+      P2[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
+    }
   }
 }
 
@@ -461,8 +514,14 @@ __global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int 
       }
       const R kappa = R(-0.5) * acc;
       const int bb = d.bid[c];
-      const R pv = (p.bubble_model && bb >= 0) ? R(d.pV[bb]) : R(p.pv0);
-      rhog[c] = R(3.0) * (pv + R(p.sigma) * kappa);
+      if constexpr (S::kDev) {
+        // rho^G - 1 = 3 (p^V - 1/3) + 3 sigma kappa, formed in FP64
+        const double pv = (p.bubble_model && bb >= 0) ? d.pV[bb] : p.pv0;
+        rhog[c] = R(3.0 * (pv - 1.0 / 3.0) + 3.0 * p.sigma * (double)kappa);
+      } else {
+        const R pv = (p.bubble_model && bb >= 0) ? R(d.pV[bb]) : R(p.pv0);
+        rhog[c] = R(3.0) * (pv + R(p.sigma) * kappa);
+      }
       nhat[3LL * c + 0] = nh(0, i, j, k);
       nhat[3LL * c + 1] = nh(1, i, j, k);
       nhat[3LL * c + 2] = nh(2, i, j, k);
@@ -490,29 +549,54 @@ constexpr int kBulkBlock = 256;
 
 template <int Q, class S, int COLL>
 __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
-                                          uint8_t fl, bool general);
+                                          uint8_t fl, bool general, bool wrap);
 
-// Persistent sweep: each warp takes 32-cell segments of the liquid segment
-// list (consecutive cells of the SoA slices, so loads and stores coalesce).
+// Persistent sweep: each warp takes 32 / kSegCells groups of the liquid
+// group list (runs of consecutive cells of the SoA slices, so loads and
+// stores coalesce per group).  Gas and obstacle lanes that share a 32-byte
+// sector of a PDF slice with a liquid lane store zero PDFs (their values are
+// never read): the sector is then written whole, which spares HBM a
+// read-modify-write of it.  Interface lanes store nothing (the interface
+// kernel writes them concurrently).
+#ifndef FSLBM_BULK_FILL
+#define FSLBM_BULK_FILL 1
+#endif
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? 4 : 2))
+__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
     k_bulk(DPtrs d, KParams p, int parity) {
+  using T = typename S::T;
+  using R = typename S::Real;
+  constexpr int kGroups = 32 / kSegCells;
+  constexpr int kFill = (32 / (int)sizeof(T)) < kSegCells ? (32 / (int)sizeof(T)) : kSegCells;
   const int nseg = d.counts[5];
   const int warps = (gridDim.x * kBulkBlock) >> 5;
   const int lane = threadIdx.x & 31;
-  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w < nseg; w += warps) {
-    const int c = d.segs[w] * 32 + lane;
-    const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_GAS;
-    const bool liq = (fl & F_TYPE) == T_LIQ;
+  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps) {
+    const int e = w * kGroups + lane / kSegCells;
+    const int c = e < nseg ? d.segs[e] * kSegCells + (lane % kSegCells) : p.N;
+    const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_IFACE;
+    const int t = fl & F_TYPE;
+    const bool liq = t == T_LIQ;
     // the whole warp takes the general path when one of its cells needs it
     const bool general = __any_sync(0xffffffffu, liq && (fl & (F_NEAR_WALL | F_WRAP)));
-    if (liq) bulk_cell<Q, S, COLL>(d, p, parity, c, fl, general);
+    const bool wrap = __any_sync(0xffffffffu, liq && (fl & F_WRAP));
+    const unsigned lm = __ballot_sync(0xffffffffu, liq);
+    if (liq) {
+      bulk_cell<Q, S, COLL>(d, p, parity, c, fl, general, wrap);
+    } else if (FSLBM_BULK_FILL) {
+      const unsigned grp = (lm >> (lane & ~(kFill - 1))) & ((1u << kFill) - 1u);
+      if (grp && t != T_IFACE) {
+        T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
+      }
+    }
   }
 }
 
 template <int Q, class S, int COLL>
 __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
-                                          uint8_t fl, bool general) {
+                                          uint8_t fl, bool general, bool wrap) {
   using R = typename S::Real;
   using T = typename S::T;
   const T* __restrict__ A = (const T*)d.pdf[parity];
@@ -522,7 +606,16 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
   if (!general) {
     const T* Ac = A + c;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = S::load(Ac[p.dofs[i]], W<Q, R>(i));
+    for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(Ac[p.dofs[i]], i);
+  } else if (!wrap) {
+    // bounce-back directions from the static wall mask
+    const uint32_t wm = (fl & F_NEAR_WALL) ? d.wallmask[c] : 0u;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const bool bb = (wm >> i) & 1u;
+      const long long idx = bb ? (long long)OPP(i) * Np + c : p.dofs[i] + c;
+      f[i] = load_w<S, Q>(A[idx], i);
+    }
   } else {
     // bounce-back directions from the static wall mask; pull sources across
     // periodic faces by branch-free index corrections
@@ -540,14 +633,14 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
                        (CZ(i) == 1 ? czp : CZ(i) == -1 ? czm : 0);
       const long long idx = ((wm >> i) & 1u) ? (long long)OPP(i) * Np + c
                                               : (long long)i * Np + (c - p.off[i] + corr);
-      f[i] = S::load(A[idx], W<Q, R>(((wm >> i) & 1u) ? OPP(i) : i));
+      f[i] = load_w<S, Q>(A[idx], i);
     }
   }
   bool bad = false;
   collide_any<Q, S, COLL>(f, p, bad);
   T* Bc = B + c;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Bc[(long long)i * Np] = S::store(f[i], W<Q, R>(i));
+  for (int i = 0; i < Q; ++i) Bc[(long long)i * Np] = store_w<S, Q>(f[i], i);
   if (bad) d.err[0] = 1;
 }
 
@@ -585,7 +678,7 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
     R fx[Q], f[Q];
     unsigned miss = 0u;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fx[i] = S::load(A[(long long)i * Np + c], W<Q, R>(i));
+    for (int i = 0; i < Q; ++i) fx[i] = load_w<S, Q>(A[(long long)i * Np + c], i);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int st = nt[OPP(i)];
@@ -593,11 +686,13 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
       if (st == T_GAS) miss |= 1u << i;
       const bool fluid = (st == T_LIQ || st == T_IFACE);
       const T v = A[(long long)(fluid ? i : OPP(i)) * Np + (fluid ? src : c)];
-      f[i] = S::load(v, W<Q, R>(fluid ? i : OPP(i)));
+      f[i] = load_w<S, Q>(v, i);
       if (st == T_GAS) f[i] = R(0.0);
     }
     // mass exchange with the streamed (not yet reconstructed) PDFs:
-    // a = f*_ibar(x + c_i) equals the pulled f_ibar(x)
+    // a = f*_ibar(x + c_i) equals the pulled f_ibar(x).  With deviations the
+    // differences are taken in FP64 on the stored values (w_i = w_ibar
+    // cancels), so a liquid neighbour's PDF sum changes by exactly -dm_i.
     const double phic = d.phi[c];
     const int clc = d.cls[c];
     double dm = 0.0;
@@ -607,22 +702,38 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
       if (ntp == T_GAS || ntp == T_OBST) continue;
       const R a = f[OPP(i)];
       const R b = fx[i];
-      if (ntp == T_LIQ) {
-        dm = dm + (double)(a - b);
+      if constexpr (S::kDev) {
+        const double ad = (double)a, bd = (double)b, w = W<Q, double>(i);
+        if (ntp == T_LIQ) {
+          dm = dm + (ad - bd);
+        } else {
+          const int cln = d.cls[nid[i]];
+          double v;
+          if (clc == cln) v = ad - bd;
+          else if (clc == CL_STD) v = (cln == CL_NF) ? ad + w : -(bd + w);
+          else if (clc == CL_NF) v = -(bd + w);
+          else v = ad + w;
+          dm = dm + 0.5 * (phic + d.phi[nid[i]]) * v;
+        }
       } else {
-        const int cln = d.cls[nid[i]];
-        R v;
-        if (clc == cln) v = a - b;
-        else if (clc == CL_STD) v = (cln == CL_NF) ? a : -b;
-        else if (clc == CL_NF) v = -b;
-        else v = a;
-        dm = dm + 0.5 * (phic + d.phi[nid[i]]) * (double)v;
+        if (ntp == T_LIQ) {
+          dm = dm + (double)(a - b);
+        } else {
+          const int cln = d.cls[nid[i]];
+          R v;
+          if (clc == cln) v = a - b;
+          else if (clc == CL_STD) v = (cln == CL_NF) ? a : -b;
+          else if (clc == CL_NF) v = -b;
+          else v = a;
+          dm = dm + 0.5 * (phic + d.phi[nid[i]]) * (double)v;
+        }
       }
     }
     const double mn = d.mass[c] + dm;
     // BC velocity from the cell's own post-collision PDFs
     R rc, jx, jy, jz;
     sums<Q, R>(fx, rc, jx, jy, jz);
+    if constexpr (S::kDev) rc = R(1.0) + rc;
     const R ux = jx / rc - R(0.5) * R(p.g[0]);
     const R uy = jy / rc - R(0.5) * R(p.g[1]);
     const R uz = jz / rc - R(0.5) * R(p.g[2]);
@@ -630,7 +741,7 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
     const R n0 = nhat[3LL * c], n1 = nhat[3LL * c + 1], n2 = nhat[3LL * c + 2];
     int v = p.variant;
     if (v == 4) v = (__popc(miss) >= 3) ? 3 : p.om3_fb;
-    const R rg = rhog[c];
+    const R rg = rhog[c];  // rho^G (FP64 engine) or rho^G - 1
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       bool rec = (miss >> i) & 1u;
@@ -639,16 +750,34 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
       if (v == 2 && dot > R(0.0)) rec = true;
       if (rec) {
         const int j = OPP(i);
-        f[i] = (feq_i<Q, R>(i, rg, ux, uy, uz) + feq_i<Q, R>(j, rg, ux, uy, uz)) - fx[j];
+        if constexpr (S::kDev) {
+          const R rgf = R(1.0) + rg;
+          f[i] = (feq_dev<Q, R>(i, rg, rgf, ux, uy, uz) + feq_dev<Q, R>(j, rg, rgf, ux, uy, uz)) - fx[j];
+        } else {
+          f[i] = (feq_i<Q, R>(i, rg, ux, uy, uz) + feq_i<Q, R>(j, rg, ux, uy, uz)) - fx[j];
+        }
       }
     }
-    const R rho = collide_any<Q, S, COLL>(f, p, bad);
+    double rho = collide_any<Q, S, COLL>(f, p, bad);
+    if constexpr (S::kDev) {
+      // the density as the stored PDFs hold it (FP64 sum of stored values):
+      // the mass a conversion to liquid hands over to the PDFs
+      double sd = 0.0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = S::store(f[i], W<Q, R>(i));
-    const double phin = mn / (double)rho;
+      for (int i = 0; i < Q; ++i) {
+        const T v = S::stored(f[i]);
+        B[(long long)i * Np + c] = v;
+        sd += (double)S::loadd(v);
+      }
+      rho = 1.0 + sd;
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
+    }
+    const double phin = mn / rho;
     d.m_next[k] = mn;
     d.phi_next[k] = phin;
-    d.rho_band[k] = (double)rho;
+    d.rho_band[k] = rho;
     d.mark[c] = (phin > 1.0 + p.eps) ? CV_TOL : (phin < -p.eps) ? CV_TOG : CV_NONE;
   }
   if (bad) d.err[0] = 1;
@@ -790,9 +919,10 @@ __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
         if (nt == T_IFACE) use = d.cfin[nb] != CV_TOG;   // stays interface or turns liquid
         if (nt == T_LIQ) use = d.claim[nb] == 0;         // stays liquid
         if (!use) continue;
-        R rn, un[3];
+        double rn;
+        R un[3];
         post_moments<Q, S>(B, Np, nb, p, rn, un);
-        sr = sr + (double)rn;
+        sr = sr + rn;
         sx = sx + (double)un[0];
         sy = sy + (double)un[1];
         sz = sz + (double)un[2];
@@ -805,18 +935,26 @@ __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
         ub1 = sy / (double)cnt;
         ub2 = sz / (double)cnt;
       }
+      if constexpr (S::kDev) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
-        B[(long long)i * Np + c] = S::store(feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2)), W<Q, R>(i));
+        for (int i = 0; i < Q; ++i)
+          B[(long long)i * Np + c] =
+              S::stored(feq_dev<Q, R>(i, R(rb - 1.0), R(rb), R(ub0), R(ub1), R(ub2)));
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          B[(long long)i * Np + c] = S::store(feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2)), W<Q, R>(i));
+      }
       const double m = 0.0 + s;
       d.mass[c] = m;
       d.phi[c] = m / rb;
     } else {  // from liquid
-      R rn, un[3];
+      double rn;
+      R un[3];
       post_moments<Q, S>(B, Np, c, p, rn, un);
-      const double m = (double)rn + s;
+      const double m = rn + s;
       d.mass[c] = m;
-      d.phi[c] = m / (double)rn;
+      d.phi[c] = m / rn;
       int best = -1;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
@@ -855,10 +993,10 @@ __device__ __forceinline__ void mark_tile(const DPtrs& d, const KParams& p, int 
   if (fresh) list[pos] = tile;
 }
 
-// Adds the 32-cell segment of cell c (c < 0: none) to the liquid segment list
-// once; every lane of the warp must call it.
+// Adds the kSegCells-cell group of cell c (c < 0: none) to the liquid group
+// list once; every lane of the warp must call it.
 __device__ __forceinline__ void mark_seg(const DPtrs& d, int c) {
-  const int seg = c >= 0 ? (c >> 5) : -1;
+  const int seg = c >= 0 ? (c / kSegCells) : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, seg);
   const bool lead = seg >= 0 && (int)(threadIdx.x & 31u) == __ffs(peers) - 1;
   const bool fresh = lead && atomicExch(&d.seg_mark[seg], 1) == 0;
@@ -866,15 +1004,17 @@ __device__ __forceinline__ void mark_seg(const DPtrs& d, int c) {
   if (fresh) d.segs[pos] = seg;
 }
 
-// Initial liquid segment list (blocks of 256 cover whole segments).
+// Initial liquid group list (blocks of 256 cover whole groups).
 static __global__ void k_segs_init(DPtrs d, KParams p) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const bool liq = c < p.N && (d.flags[c] & F_TYPE) == T_LIQ;
-  const bool any = __any_sync(0xffffffffu, liq);
-  const bool fresh = any && (threadIdx.x & 31) == 0;
-  if (fresh) d.seg_mark[c >> 5] = 1;
+  const unsigned b = __ballot_sync(0xffffffffu, liq);
+  const unsigned gmask = kSegCells == 32 ? 0xffffffffu : ((1u << kSegCells) - 1u);
+  const bool fresh = (lane % kSegCells) == 0 && ((b >> lane) & gmask) != 0;
+  if (fresh) d.seg_mark[c / kSegCells] = 1;
   const int pos = warp_append(&d.counts[5], fresh);
-  if (fresh) d.segs[pos] = c >> 5;
+  if (fresh) d.segs[pos] = c / kSegCells;
 }
 
 // Tile list of an interface list (initial state and checkpoint load).
@@ -983,12 +1123,13 @@ __global__ void __launch_bounds__(kBlock) k_obs_partial(DPtrs d, KParams p, int 
     const int t = d.flags[c] & F_TYPE;
     cnt[t] += 1.0;
     if (t == T_LIQ || t == T_IFACE) {
-      R r, u[3];
+      double r;
+      R u[3];
       post_moments<Q, S>(P, p.Np, c, p, r, u);
       const double uu = sqrt((double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
-      if (!(uu == uu) || !(r > R(0.0))) nan = 1.0;
+      if (!(uu == uu) || !(r > 0.0)) nan = 1.0;
       if (uu > umax) umax = uu;
-      mass += (t == T_LIQ) ? (double)r : d.mass[c];
+      mass += (t == T_LIQ) ? r : d.mass[c];
       vol += d.phi[c];
       if (!(d.mass[c] == d.mass[c])) nan = 1.0;
     }
@@ -1035,8 +1176,14 @@ __global__ void k_pdf_out(DPtrs d, KParams p, int parity, double* out) {
   const int t = d.flags[c] & F_TYPE;
   const bool fluid = (t == T_LIQ || t == T_IFACE);
 #pragma unroll
-  for (int i = 0; i < Q; ++i)
-    out[(long long)i * p.N + c] = fluid ? (double)S::load(P[(long long)i * p.Np + c], W<Q, R>(i)) : 0.0;
+  for (int i = 0; i < Q; ++i) {
+    double v;
+    if constexpr (S::kDev)
+      v = (double)S::loadd(P[(long long)i * p.Np + c]) + W<Q, double>(i);
+    else
+      v = (double)S::load(P[(long long)i * p.Np + c], W<Q, R>(i));
+    out[(long long)i * p.N + c] = fluid ? v : 0.0;
+  }
 }
 
 }  // namespace fslbm

@@ -1,0 +1,108 @@
+"""Parity at the benchmark's full size: the rising Taylor bubble, 160 x 160 x
+1024 cells (26.2 M), D3Q19 TRT, variant OM, curvature-driven Laplace pressure
+and the bubble model, launched as the benchmark launches it (CUDA-graph steps
+on a torch stream, the bulk sweep forked onto a side stream).
+
+The oracle runs the whole domain for a few steps (a few seconds per step on
+one host thread); every cell is compared.
+
+* FP64 mode: identical flags, PDFs / fill levels / masses within 1e-12
+  relative, bubble volume and pressure within 1e-13 relative.
+* FP32 mode (the benchmark's precision): identical flags, and PDFs, fill
+  levels and masses within the FP32 bound derived below.
+
+FP32 bound.  With unit roundoff u = 2^-24 (6.0e-8), one step rounds each
+stored PDF once on store and forms rho and j from q = 19 terms of size <= 1/3
+(error <= 19 u rho), from which f^eq and the update are formed with a few more
+roundings of O(1) values; per step the error of a PDF is below ~25 u (1.5e-6
+bound, far less in practice).  Over STEPS = 2 steps: 3e-6 absolute on PDFs.
+The interface mass gains sum_i (f_in - f_out) over 18 directions of FP32 PDFs
+per step: error <= 2 * 18 * 25 u per step, 1e-4 over 2 steps; fill = m / rho
+inherits it.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2207_13962_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 2
+PDF_TOL32 = 3e-6
+FILL_TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def taylor():
+    sc = S.taylor_bubble(variant="OM")
+    o = Oracle(*sc.shape, **S.make_oracle_kwargs(sc))
+    o.init(sc.fill, sc.flags, sc.velocity, sc.density)
+    V0, P0, _ = o.bubbles()
+    o.step(STEPS)
+    r = o.read()
+    V, P, _ = o.bubbles()
+    M = o.total_mass()
+    del o
+    return sc, r, (V0, P0), (V, P), M
+
+
+def _gpu_run(sc, precision):
+    import torch
+
+    from paper_2207_13962_gb300 import fslbm
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    g = fslbm.context_for(sc, precision=precision, stream=stream.cuda_stream)
+    g.step(STEPS)
+    assert g.sync() == 0
+    r = g.read()
+    V, P = g.bubbles()
+    obs = g.observables()
+    g.close()
+    return r, (V, P), obs
+
+
+def test_taylor_bubble_full_size_fp64_every_cell(taylor, gpu_lib):
+    sc, ro, (V0, _), (Vo, Po), M = taylor
+    rg, (Vg, Pg), obs = _gpu_run(sc, "FP64")
+    np.testing.assert_array_equal(rg["flags"], ro["flags"])
+    fl = ro["flags"]
+    fluid = (fl == S.LIQ) | (fl == S.IFACE)
+    iface = fl == S.IFACE
+    tol = lambda b: 1e-12 * np.maximum(1.0, np.abs(b))
+    assert np.all(np.abs(rg["fill"] - ro["fill"]) <= tol(ro["fill"]))
+    assert np.all(np.abs(rg["mass"][iface] - ro["mass"][iface]) <= tol(ro["mass"][iface]))
+    for i in range(sc.q):  # one direction slice at a time (4 GB per field)
+        a, b = rg["pdf"][i][fluid], ro["pdf"][i][fluid]
+        assert np.all(np.abs(a - b) <= tol(b)), f"pdf direction {i}"
+    assert len(Vg) == len(Vo) == 1
+    np.testing.assert_allclose(Vg, Vo, rtol=1e-13)
+    np.testing.assert_allclose(Pg, Po, rtol=1e-13)
+    # bubble model: p^V V = p^V(0) V(0) (Eq. nm-fslbm-pressure-volume)
+    np.testing.assert_allclose(Pg * Vg, (1.0 / 3.0) * V0, rtol=1e-14)
+    assert abs(obs["total_mass"] - M) <= 1e-12 * M
+
+
+def test_taylor_bubble_full_size_fp32_every_cell(taylor, gpu_lib):
+    sc, ro, _, (Vo, Po), M = taylor
+    rg, (Vg, Pg), obs = _gpu_run(sc, "FP32")
+    np.testing.assert_array_equal(rg["flags"], ro["flags"])
+    fl = ro["flags"]
+    fluid = (fl == S.LIQ) | (fl == S.IFACE)
+    iface = fl == S.IFACE
+    dfill = np.abs(rg["fill"] - ro["fill"]).max()
+    dmass = np.abs(rg["mass"][iface] - ro["mass"][iface]).max()
+    assert dfill <= FILL_TOL32 and dmass <= FILL_TOL32, (dfill, dmass)
+    worst = 0.0
+    for i in range(sc.q):
+        worst = max(worst, float(np.abs(rg["pdf"][i][fluid] - ro["pdf"][i][fluid]).max()))
+    assert worst <= PDF_TOL32, worst
+    # V = #gas + sum over interface cells of (1 - phi) in 2^-32 fixed point:
+    # the FP32 run's volume differs by at most the summed fill-level error
+    bound = np.abs(rg["fill"][iface] - ro["fill"][iface]).sum() + iface.sum() * 2.0 ** -32
+    assert abs(Vg[0] - Vo[0]) <= bound, (Vg, Vo, bound)
+    np.testing.assert_allclose(Pg * Vg, Po * Vo, rtol=1e-14)  # p^V V = p^V(0) V(0)
+    print(f"FP32 vs FP64 oracle, Taylor bubble 160x160x1024, {STEPS} steps: pdf {worst:.2e} "
+          f"fill {dfill:.2e} mass {dmass:.2e} volume {abs(Vg[0] - Vo[0]) / Vo[0]:.2e} (rel)")
+    assert abs(obs["total_mass"] - M) / M <= 1e-6
