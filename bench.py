@@ -250,8 +250,8 @@ def bench_ours(args, ws, rank, local):
     n_liq = 0.5 * (obs1["n_liquid"] + obs2["n_liquid"])
     nseg = ctx.work_counts()["liquid_segments"]
     # algorithmic bytes of one bulk launch: read + write q PDFs per liquid
-    # cell, one flag byte per cell of the swept 8-cell groups
-    alg_bytes = n_liq * 2 * Q * S_BYTES[prec] + nseg * 8
+    # cell, one flag byte per cell of the swept 32-cell groups
+    alg_bytes = n_liq * 2 * Q * S_BYTES[prec] + nseg * 32
     achieved = alg_bytes / (bulk_ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))

@@ -175,7 +175,7 @@ fslbm_status fslbm_load(fslbm_ctx* ctx, const void* buf, size_t size);
 fslbm_status fslbm_interface_count(fslbm_ctx* ctx, int64_t* n);
 
 /* Sizes of the work lists of the next step (synchronizes; any pointer may be
- * NULL): interface cells, 8-cell groups swept by the bulk kernel (those
+ * NULL): interface cells, 32-cell groups swept by the bulk kernel (those
  * that hold or held liquid) and 8^3 geometry tiles holding interface cells. */
 fslbm_status fslbm_work_counts(fslbm_ctx* ctx, int64_t* interface_cells,
                                int64_t* liquid_segments, int64_t* geometry_tiles);
@@ -204,6 +204,57 @@ fslbm_status fslbm_observables_noalloc(const fslbm_domain* domain, int q, const 
 void fslbm_destroy(fslbm_ctx* ctx);
 const char* fslbm_last_error(const fslbm_ctx* ctx);
 const char* fslbm_version(void);
+
+/* ------------------------------------------------------------------ batches
+ * Many domains of different sizes advance together: each phase of the step
+ * (geometry, bulk stream-collide, interface update, conversion, excess mass,
+ * bubbles; Sec. 2.2, 3) runs as ONE launch over a block table of all member
+ * domains, captured once in a CUDA graph.  Results are the same as stepping
+ * each member alone (same kernels, bitwise).
+ *
+ * Members are initialized contexts of the same lattice, precision and
+ * collision operator (variant, omega, g, sigma, eps_phi, bubble model and
+ * sizes may differ).  They stay owned by the caller, must outlive the batch,
+ * and keep working with every single-context call between batch steps
+ * (fslbm_step, fslbm_read_fields, ...): a batch step is ordered after the
+ * members' pending work and their later work after it. */
+typedef struct fslbm_batch fslbm_batch;
+
+/* Launch shape of a batch step: persistent bulk-sweep blocks per SM and
+ * interface-band blocks per SM; ms_per_step is the time measured for it by
+ * fslbm_batch_autotune (0 if not measured). */
+typedef struct {
+  int bulk_blocks_per_sm;
+  int band_blocks_per_sm;
+  double ms_per_step;
+} fslbm_tuning;
+
+/* Group n >= 1 members (host array of context pointers, copied).  Work is
+ * enqueued on stream (cudaStream_t, NULL = legacy default).  FSLBM_ESTATE if
+ * a member is not initialized; FSLBM_EINVAL for mixed lattice, precision or
+ * collision, or a member listed twice. */
+fslbm_status fslbm_batch_create(fslbm_ctx* const* members, int n, void* stream, fslbm_batch** out);
+
+/* Advance every member n >= 0 steps (asynchronous, n graph launches). */
+fslbm_status fslbm_batch_step(fslbm_batch* b, int n);
+
+/* Wait for the batch stream; FSLBM_EUNSTABLE if any member flagged an
+ * instability.  member_status (n entries, may be NULL) receives each
+ * member's status. */
+fslbm_status fslbm_batch_sync(fslbm_batch* b, fslbm_status* member_status);
+
+/* Pick the launch shape by measurement: every combination of 1..max bulk
+ * blocks per SM and {1, 2, 4, 8} band blocks per SM runs 1 + steps batch
+ * steps timed with CUDA events; the fastest is kept and returned in *chosen
+ * (may be NULL).  The steps are real steps: every member advances by
+ * (steps + 1) x (number of candidates). */
+fslbm_status fslbm_batch_autotune(fslbm_batch* b, int steps, fslbm_tuning* chosen);
+fslbm_status fslbm_batch_set_tuning(fslbm_batch* b, const fslbm_tuning* t);
+fslbm_status fslbm_batch_get_tuning(const fslbm_batch* b, fslbm_tuning* t);
+/* Kernels launched by batch steps so far. */
+fslbm_status fslbm_batch_launches(const fslbm_batch* b, int64_t* n);
+void fslbm_batch_destroy(fslbm_batch* b);
+const char* fslbm_batch_last_error(const fslbm_batch* b);
 
 #ifdef __cplusplus
 }

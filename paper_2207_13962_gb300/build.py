@@ -24,6 +24,7 @@ SOURCES = {
     "fslbm_f32.cu": [],
     "fslbm_f16.cu": [],
     "fslbm_noalloc.cu": [],
+    "fslbm_batch.cu": [],
 }
 
 

@@ -11,47 +11,14 @@
 #include <vector>
 
 #include "../../include/fslbm.h"
-#include "fslbm_internal.h"
+#include "fslbm_ctx.h"
 #include "fslbm_kernels.cuh"
 
 using namespace fslbm;
 
-struct fslbm_ctx {
-  fslbm_domain dom;
-  int q = 19, collision = 1, variant = 3;
-  fslbm_params prm;
-  KParams kp;
-  DPtrs d;
-  Ops ops;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  Fork fork{nullptr, nullptr, nullptr};
-  int bulk_grid = 608;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int parity = 0;
-  int64_t step = 0;
-  bool initialized = false;
-  int band_grid = 608;
-  bool timing = false;
-  StageEvents ev;
-  bool ev_made = false;
-  double stage_ms[5] = {0, 0, 0, 0, 0};
-  long long launches = 0;
-  double* d_obs = nullptr;
-  std::vector<void*> allocs;
-  std::string err;
-};
 
-namespace {
 
-const char* kVersion = "fslbm-gb300 1.0";
-
-#ifndef FSLBM_BAND_PRIO
-#define FSLBM_BAND_PRIO 1
-#endif
-#ifndef FSLBM_BULK_RESERVE
-#define FSLBM_BULK_RESERVE 0
-#endif
+namespace fslbm {
 
 fslbm_status fail(fslbm_ctx* c, fslbm_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -62,6 +29,50 @@ fslbm_status cuda_fail(fslbm_ctx* c, cudaError_t e, const char* where) {
   return fail(c, e == cudaErrorMemoryAllocation ? FSLBM_ENOMEM : FSLBM_ECUDA,
               std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+// The interface-band kernels form a chain of short, latency-bound launches
+// that runs beside the bulk sweep on a forked stream.  Their graph nodes get
+// the device's highest priority, so that the block scheduler places their
+// blocks first whenever an SM has room.  Nodes of skip0 / skip1 (the bulk
+// sweep) keep the default priority.
+cudaError_t prioritise_nodes(cudaGraph_t g, const void* skip0, const void* skip1) {
+#if FSLBM_BAND_PRIO
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return e;
+  size_t n = 0;
+  e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess || n == 0) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  e = cudaGraphGetNodes(g, nodes.data(), &n);
+  for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[i], &t);
+    if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+    if (e != cudaSuccess) break;
+    if (kp.func == skip0 || kp.func == skip1) continue;
+    cudaLaunchAttributeValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.priority = greatest;
+    e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
+  }
+  return e;
+#else
+  (void)g;
+  (void)skip0;
+  (void)skip1;
+  return cudaSuccess;
+#endif
+}
+
+}  // namespace fslbm
+
+namespace {
+
+const char* kVersion = "fslbm-gb300 1.0";
+
 
 template <class T>
 cudaError_t dalloc(fslbm_ctx* c, T** p, size_t bytes) {
@@ -92,42 +103,6 @@ void destroy_graphs(fslbm_ctx* c) {
     }
 }
 
-// The interface-band kernels form a chain of short, latency-bound launches
-// that runs beside the bulk sweep on a forked stream; giving their graph
-// nodes the device's highest priority lets the block scheduler place their
-// blocks first whenever an SM has room, so the chain finishes under the
-// bandwidth-bound sweep instead of after it.
-cudaError_t prioritise_band(fslbm_ctx* c, cudaGraph_t g) {
-#if FSLBM_BAND_PRIO
-  int least = 0, greatest = 0;
-  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  if (e != cudaSuccess) return e;
-  size_t n = 0;
-  e = cudaGraphGetNodes(g, nullptr, &n);
-  if (e != cudaSuccess || n == 0) return e;
-  std::vector<cudaGraphNode_t> nodes(n);
-  e = cudaGraphGetNodes(g, nodes.data(), &n);
-  for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
-    cudaGraphNodeType t;
-    e = cudaGraphNodeGetType(nodes[i], &t);
-    if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
-    cudaKernelNodeParams kp;
-    e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
-    if (e != cudaSuccess) break;
-    if (kp.func == c->ops.bulk_fn[0] || kp.func == c->ops.bulk_fn[1]) continue;
-    cudaLaunchAttributeValue v;
-    std::memset(&v, 0, sizeof(v));
-    v.priority = greatest;
-    e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
-  }
-  return e;
-#else
-  (void)c;
-  (void)g;
-  return cudaSuccess;
-#endif
-}
-
 cudaError_t build_graphs(fslbm_ctx* c) {
   destroy_graphs(c);
   for (int par = 0; par < 2; ++par) {
@@ -137,7 +112,7 @@ cudaError_t build_graphs(fslbm_ctx* c) {
     c->ops.step(c->d, c->kp, par, c->band_grid, c->bulk_grid, c->cap_stream, nullptr, &c->fork);
     e = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) return e;
-    e = prioritise_band(c, g);
+    e = prioritise_nodes(g, c->ops.bulk_fn[0], c->ops.bulk_fn[1]);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[par], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return e;

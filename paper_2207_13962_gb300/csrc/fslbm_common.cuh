@@ -154,11 +154,13 @@ inline FastDiv make_fastdiv(unsigned d) {
 constexpr int kBulkMinBlocks32 = FSLBM_BULK_MINB;
 
 // Granularity of the bulk sweep's work list: groups of kSegCells consecutive
-// cells that hold liquid (8 = one 32-byte sector of an FP32 PDF slice).  A
-// warp takes 32 / kSegCells groups, so lanes are spent on liquid cells rather
-// than on the gas, obstacle and interface cells around them.
+// cells that hold liquid; a warp takes 32 / kSegCells groups.  32 keeps each
+// warp-wide load one contiguous 128-byte row of a PDF slice: smaller groups
+// raise lane occupancy on ragged liquid regions but split every load into
+// separate sectors, which measured slower on GB300 (0.82 vs 0.59 ms per sweep
+// of the 160 x 160 x 1024 Taylor bubble for 8-cell groups).
 #ifndef FSLBM_SEG_CELLS
-#define FSLBM_SEG_CELLS 8
+#define FSLBM_SEG_CELLS 32
 #endif
 constexpr int kSegCells = FSLBM_SEG_CELLS;
 static_assert(kSegCells == 8 || kSegCells == 16 || kSegCells == 32, "segment size");
@@ -215,6 +217,27 @@ struct DPtrs {
   int* err;      // [0] instability seen
   double* red;   // observable partials
   int red_blocks;
+};
+
+// One domain of a batch (a block-table entry): device pointers, parameters
+// and the parity of the PDF buffer that holds its current state.
+struct DomRec {
+  DPtrs d;
+  KParams p;
+  int parity;
+};
+
+// Prefix offsets (n + 1 entries each, device memory) of the domains' work in
+// the units of each batched kernel, recomputed on the device every step:
+//   tiles: geometry tiles; bulk: warp units of the bulk sweep;
+//   band: interface cells rounded up to a multiple of 32 (warp-aligned);
+//   all: interface + new interface cells rounded up to a multiple of 32.
+struct BatchPlan {
+  int n;
+  int* tiles;
+  int* bulk;
+  int* band;
+  int* all;
 };
 
 }  // namespace fslbm

@@ -60,6 +60,33 @@ struct Engine {
     if (ev) ev->mark(5, st);
   }
 
+  // One step of all domains of a block table.  Same stages and stream fork
+  // as step(); the plan kernels lay out each phase's work on the device, and
+  // the last kernel swaps every domain's buffers.
+  static void batch_step(DomRec* recs, const BatchPlan& pl, int band_grid, int bulk_grid,
+                         int collision, cudaStream_t st, const Fork* fk) {
+    kb_plan_front<<<1, 1024, 0, st>>>(recs, pl);
+    cudaEventRecord(fk->fork, st);
+    cudaStreamWaitEvent(fk->side, fk->fork, 0);
+    if (collision == 0)
+      kb_bulk<Q, S, 0><<<bulk_grid, kBulkBlock, 0, fk->side>>>(recs, pl);
+    else
+      kb_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, fk->side>>>(recs, pl);
+    cudaEventRecord(fk->join, fk->side);
+    kb_geometry<Q, S><<<band_grid, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(recs, pl);
+    if (collision == 0)
+      kb_interface<Q, S, 0><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+    else
+      kb_interface<Q, S, 1><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+    kb_resolve<Q><<<band_grid, kBlock, 0, st>>>(recs, pl);
+    kb_count<Q><<<band_grid, kBlock, 0, st>>>(recs, pl);
+    kb_plan_back<<<1, 1024, 0, st>>>(recs, pl);
+    cudaStreamWaitEvent(st, fk->join, 0);
+    kb_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+    kb_finalize<<<band_grid, kBlock, 0, st>>>(recs, pl);
+    kb_bubble_end<<<pl.n, 256, 0, st>>>(recs);
+  }
+
   static void observables(const DPtrs& d, const KParams& p, int parity, double* out,
                           cudaStream_t st) {
     k_obs_partial<Q, S><<<d.red_blocks, kBlock, 0, st>>>(d, p, parity, d.red);
@@ -73,6 +100,8 @@ struct Engine {
   static Ops ops() {
     cudaFuncSetAttribute(k_geometry<Q, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)geometry_smem<typename S::Real>());
+    cudaFuncSetAttribute(kb_geometry<Q, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)geometry_smem<typename S::Real>());
     Ops o;
     o.init_cells = &init_cells;
     o.init_check = &init_check;
@@ -83,6 +112,9 @@ struct Engine {
     o.real_size = sizeof(typename S::Real);
     o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
     o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
+    o.batch_step = &batch_step;
+    o.batch_bulk_fn[0] = (const void*)&kb_bulk<Q, S, 0>;
+    o.batch_bulk_fn[1] = (const void*)&kb_bulk<Q, S, 1>;
     return o;
   }
 };

@@ -36,6 +36,10 @@ struct Ops {
   size_t real_size;
   const void* bulk_fn[2];  // the bulk sweep kernels (SRT, TRT): graph nodes of
                            // every other kernel get the higher priority
+  // one step of every domain of a block table (see DomRec, BatchPlan)
+  void (*batch_step)(DomRec* recs, const BatchPlan& plan, int band_grid, int bulk_grid,
+                     int collision, cudaStream_t, const Fork*);
+  const void* batch_bulk_fn[2];
 };
 
 // Defined in fslbm_f64.cu, fslbm_f32.cu, fslbm_f16.cu.

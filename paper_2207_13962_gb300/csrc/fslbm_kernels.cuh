@@ -393,27 +393,20 @@ constexpr size_t geometry_smem() {
   return sizeof(R) * (GB + GS * GS * GS + 3 * GN * GN * GN) + GB;
 }
 
+// One 8^3 tile of the geometry pass (every thread of the block calls it).
 template <int Q, class S>
-__global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, int tile,
+                                              unsigned char* g_smem) {
   using R = typename S::Real;
-  extern __shared__ __align__(16) unsigned char g_smem[];
   R* sphi = (R*)g_smem;
   R* sps = sphi + GB;
   R* snh = sps + GS * GS * GS;
   uint8_t* styp = (uint8_t*)(snh + 3 * GN * GN * GN);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    d.counts[parity ^ 1] = 0;      // next band list
-    d.counts[2] = 0;               // new-cell list
-    d.counts[3 + (parity ^ 1)] = 0;  // next tile list
-  }
-  const int ntiles = d.counts[3 + parity];
-  const int* __restrict__ tiles = d.tiles[parity];
   const int ntx = (p.nx + GT - 1) / GT, nty = (p.ny + GT - 1) / GT;
   R* nhat = (R*)d.nhat;
   R* rhog = (R*)d.rhog;
   const R wsum = R(3.6796875);
-  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-    const int tile = tiles[tt];
+
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const int ox = tx * GT - 3, oy = ty * GT - 3, oz = tz * GT - 3;
     __syncthreads();
@@ -536,6 +529,22 @@ __global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int 
     }
     if (threadIdx.x == 0) d.tile_mark[tile] = 0;
   }
+
+// Resets the work-list counters that this step fills (next band list, new
+// cells, next tile list).
+__device__ __forceinline__ void reset_step_counts(const DPtrs& d, int parity) {
+  d.counts[parity ^ 1] = 0;
+  d.counts[2] = 0;
+  d.counts[3 + (parity ^ 1)] = 0;
+}
+
+template <int Q, class S>
+__global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int parity) {
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) reset_step_counts(d, parity);
+  const int ntiles = d.counts[3 + parity];
+  for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x)
+    geometry_tile<Q, S>(d, p, d.tiles[parity][tt], g_smem);
 }
 
 // ------------------------------------------------------------ bulk sweep
@@ -561,17 +570,17 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
 #ifndef FSLBM_BULK_FILL
 #define FSLBM_BULK_FILL 1
 #endif
+// One warp's share of the bulk sweep: groups [w G, w G + G) of the liquid
+// group list, G = 32 / kSegCells (every lane of the warp calls it).
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
-    k_bulk(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int parity, int w,
+                                          int nseg) {
   using T = typename S::T;
   using R = typename S::Real;
   constexpr int kGroups = 32 / kSegCells;
   constexpr int kFill = (32 / (int)sizeof(T)) < kSegCells ? (32 / (int)sizeof(T)) : kSegCells;
-  const int nseg = d.counts[5];
-  const int warps = (gridDim.x * kBulkBlock) >> 5;
   const int lane = threadIdx.x & 31;
-  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps) {
+
     const int e = w * kGroups + lane / kSegCells;
     const int c = e < nseg ? d.segs[e] * kSegCells + (lane % kSegCells) : p.N;
     const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_IFACE;
@@ -592,6 +601,15 @@ __global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? k
       }
     }
   }
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
+    k_bulk(DPtrs d, KParams p, int parity) {
+  constexpr int kGroups = 32 / kSegCells;
+  const int nseg = d.counts[5];
+  const int warps = (gridDim.x * kBulkBlock) >> 5;
+  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
+    bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
 }
 
 template <int Q, class S, int COLL>
@@ -649,19 +667,18 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
 // variant's set R (Sec. 3), mass exchange (Eq. nm-fslbm-mass-flux) with
 // Thuerey's adjustment, fill update phi = m / rho, collision, marks.
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p, int parity, int k,
+                                               bool& bad) {
   using R = typename S::Real;
   using T = typename S::T;
   const int* __restrict__ band = d.band[parity];
-  const int n = d.counts[parity];
   const T* __restrict__ A = (const T*)d.pdf[parity];
   T* __restrict__ B = (T*)d.pdf[parity ^ 1];
   const long long Np = p.Np;
   const uint8_t* __restrict__ flags = d.flags;
   const R* nhat = (const R*)d.nhat;
   const R* rhog = (const R*)d.rhog;
-  bool bad = false;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+
     const int c = band[k];
     int x, y, z;
     decode(p, c, x, y, z);
@@ -780,6 +797,13 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
     d.rho_band[k] = rho;
     d.mark[c] = (phin > 1.0 + p.eps) ? CV_TOL : (phin < -p.eps) ? CV_TOG : CV_NONE;
   }
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parity) {
+  const int n = d.counts[parity];
+  bool bad = false;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    interface_cell<Q, S, COLL>(d, p, parity, k, bad);
   if (bad) d.err[0] = 1;
 }
 
@@ -788,10 +812,9 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
 // to a cell marked for liquid); claim gas neighbours of cells turning liquid
 // and liquid neighbours of cells turning gas as new interface cells.
 template <int Q>
-__global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void resolve_cell(const DPtrs& d, const KParams& p, int parity, int k) {
   const int* __restrict__ band = d.band[parity];
-  const int n = d.counts[parity];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+
     const int c = band[k];
     d.mass[c] = d.m_next[k];
     d.phi[c] = d.phi_next[k];
@@ -806,7 +829,7 @@ __global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int pari
       }
     }
     d.conv[c] = cv;
-    if (cv == CV_NONE) continue;
+    if (cv == CV_NONE) return;
     const int want = (cv == CV_TOL) ? T_GAS : T_LIQ;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -818,6 +841,12 @@ __global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int pari
       if (!(old & bit)) d.newlist[atomicAdd(&d.counts[2], 1)] = nb;
     }
   }
+
+template <int Q>
+__global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int parity) {
+  const int n = d.counts[parity];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    resolve_cell<Q>(d, p, parity, k);
 }
 
 // flag of a neighbour after conversion, before deferral
@@ -832,15 +861,14 @@ __device__ __forceinline__ bool post_iface(const DPtrs& d, int nb) {
 // Excess-mass receivers (Eq. nm-fslbm-excess-mass): interface cells after
 // conversion in the lattice neighbourhood; none -> the conversion is deferred.
 template <int Q>
-__global__ void __launch_bounds__(kBlock) k_count(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void count_cell(const DPtrs& d, const KParams& p, int parity, int k) {
   const int* __restrict__ band = d.band[parity];
-  const int n = d.counts[parity];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+
     const int c = band[k];
     const uint8_t cv = d.conv[c];
     if (cv == CV_NONE) {
       d.cfin[c] = CV_NONE;
-      continue;
+      return;
     }
     int x, y, z;
     decode(p, c, x, y, z);
@@ -856,6 +884,12 @@ __global__ void __launch_bounds__(kBlock) k_count(DPtrs d, KParams p, int parity
       d.cfin[c] = cv;
     }
   }
+
+template <int Q>
+__global__ void __launch_bounds__(kBlock) k_count(DPtrs d, KParams p, int parity) {
+  const int n = d.counts[parity];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    count_cell<Q>(d, p, parity, k);
 }
 
 __device__ __forceinline__ bool converted(const DPtrs& d, int nb) {
@@ -868,15 +902,14 @@ __device__ __forceinline__ bool converted(const DPtrs& d, int nb) {
 // interface cells from gas: f* = f^eq(mean rho, mean u) over liquid and old
 // interface neighbours; new interface cells from liquid: m = rho, phi = 1.
 template <int Q, class S>
-__global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int parity, int k) {
   using R = typename S::Real;
   using T = typename S::T;
   const int* __restrict__ band = d.band[parity];
   const int nb_ = d.counts[parity];
-  const int nn = d.counts[2];
   T* __restrict__ B = (T*)d.pdf[parity ^ 1];
   const long long Np = p.Np;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb_ + nn; k += gridDim.x * blockDim.x) {
+
     const bool is_band = k < nb_;
     const int c = is_band ? band[k] : d.newlist[k - nb_];
     int x, y, z;
@@ -886,12 +919,12 @@ __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
       if (f == CV_TOL) {
         d.phi[c] = 1.0;
         d.mass[c] = d.rho_band[k];
-        continue;
+        return;
       }
       if (f == CV_TOG) {
         d.phi[c] = 0.0;
         d.mass[c] = 0.0;
-        continue;
+        return;
       }
     }
     double s = 0.0;
@@ -904,7 +937,7 @@ __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
       const double m = d.mass[c] + s;
       d.mass[c] = m;
       d.phi[c] = m / d.rho_band[k];
-      continue;
+      return;
     }
     const int t = d.flags[c] & F_TYPE;
     if (t == T_GAS) {
@@ -968,6 +1001,12 @@ __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
       d.bid[c] = best;
     }
   }
+
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
+  const int n = d.counts[parity] + d.counts[2];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    apply_cell<Q, S>(d, p, parity, k);
 }
 
 // Fixed-point bubble-volume term round((1 - phi) 2^32).
@@ -1029,15 +1068,16 @@ static __global__ void k_tiles_of_band(DPtrs d, KParams p, int parity) {
 }
 
 // Final flags, next interface list, bubble gas counts and interface sums.
-static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, int parity) {
+// Entries [base, base + 32) of the band + new-cell list (every lane of the
+// warp calls it).
+__device__ __forceinline__ void finalize_warp(const DPtrs& d, const KParams& p, int parity,
+                                              int base) {
   const int* __restrict__ band = d.band[parity];
   int* __restrict__ next = d.band[parity ^ 1];
   const int nb_ = d.counts[parity];
   const int total = nb_ + d.counts[2];
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  for (int base = wid * 32; base < total; base += warps * 32) {
+
     const int k = base + lane;
     bool keep = false, to_liq = false;
     int c = -1, bub = -1, dgas = 0;
@@ -1095,10 +1135,16 @@ static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, 
     mark_tile(d, p, keep ? c : -1, d.tiles[parity ^ 1], &d.counts[3 + (parity ^ 1)]);
     mark_seg(d, to_liq ? c : -1);
   }
+
+static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, int parity) {
+  const int total = d.counts[parity] + d.counts[2];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int base = wid * 32; base < total; base += warps * 32) finalize_warp(d, p, parity, base);
 }
 
 // p^V_b = p^V_b(0) V_b(0) / V_b (Eq. nm-fslbm-pressure-volume).
-static __global__ void k_bubble(DPtrs d, KParams p) {
+__device__ __forceinline__ void bubble_update(const DPtrs& d, const KParams& p) {
   for (int b = threadIdx.x; b < d.nb; b += blockDim.x) {
     const long long acc = d.gas_cnt[b] * 4294967296LL + d.iface_fix[b];
     const double V = __ll2double_rn(acc) / 4294967296.0;
@@ -1107,6 +1153,8 @@ static __global__ void k_bubble(DPtrs d, KParams p) {
     d.iface_fix[b] = 0;
   }
 }
+
+static __global__ void k_bubble(DPtrs d, KParams p) { bubble_update(d, p); }
 
 // ------------------------------------------------------------ observables
 // Per-block partials: [0] mass, [1] max|u|, [2] liquid volume, [3] nan,
@@ -1184,6 +1232,173 @@ __global__ void k_pdf_out(DPtrs d, KParams p, int parity, double* out) {
       v = (double)S::load(P[(long long)i * p.Np + c], W<Q, R>(i));
     out[(long long)i * p.N + c] = fluid ? v : 0.0;
   }
+}
+
+// ---------------------------------------------------------------- batches
+// Many domains of different sizes advance in one launch per phase.  The
+// block table is an array of DomRec; the plan kernels turn each domain's
+// device-side list counts into prefix offsets, and every batched kernel maps
+// its global work index to (domain, local index) by binary search over the
+// offsets.  Domain ranges of the cell lists are padded to multiples of 32,
+// so a warp never straddles two domains and the warp-collective code of the
+// single-domain bodies runs unchanged.
+
+// Largest domain k < n with off[k] <= g (off non-decreasing, off[0] = 0).
+__device__ __forceinline__ int find_domain(const int* __restrict__ off, int n, int g) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Block-wide exclusive prefix sum of per-domain values (one block; values
+// produced by f(k) for k < n) into off[0..n].
+template <class F>
+__device__ __forceinline__ void block_prefix(int n, int* off, F f) {
+  __shared__ int carry;
+  __shared__ int wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int v = k < n ? f(k) : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wsum[lane] = t;
+    }
+    __syncthreads();
+    const int incl = x + (wid > 0 ? wsum[wid - 1] : 0) + carry;
+    if (k < n) off[k + 1] = incl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[0] = 0;
+}
+
+__device__ __forceinline__ int round32(int v) { return (v + 31) & ~31; }
+
+// Plan of the first phase (before geometry): resets the counters this step
+// fills and lays out tiles, bulk warp units and band cells.
+static __global__ void kb_plan_front(DomRec* recs, BatchPlan pl) {
+  constexpr int kGroups = 32 / kSegCells;
+  for (int k = threadIdx.x; k < pl.n; k += blockDim.x) reset_step_counts(recs[k].d, recs[k].parity);
+  __syncthreads();
+  block_prefix(pl.n, pl.tiles, [&](int k) { return recs[k].d.counts[3 + recs[k].parity]; });
+  block_prefix(pl.n, pl.bulk, [&](int k) { return (recs[k].d.counts[5] + kGroups - 1) / kGroups; });
+  block_prefix(pl.n, pl.band, [&](int k) { return round32(recs[k].d.counts[recs[k].parity]); });
+}
+
+// Plan of the second phase (after the new-cell list is complete).
+static __global__ void kb_plan_back(DomRec* recs, BatchPlan pl) {
+  block_prefix(pl.n, pl.all, [&](int k) {
+    return round32(recs[k].d.counts[recs[k].parity] + recs[k].d.counts[2]);
+  });
+}
+
+template <int Q, class S>
+__global__ void __launch_bounds__(kGeoBlock) kb_geometry(const DomRec* __restrict__ recs, BatchPlan pl) {
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  const int total = pl.tiles[pl.n];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = find_domain(pl.tiles, pl.n, t);
+    const DomRec& r = recs[k];
+    geometry_tile<Q, S>(r.d, r.p, r.d.tiles[r.parity][t - pl.tiles[k]], g_smem);
+  }
+}
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
+    kb_bulk(const DomRec* __restrict__ recs, BatchPlan pl) {
+  const int total = pl.bulk[pl.n];
+  const int warps = (gridDim.x * kBulkBlock) >> 5;
+  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w < total; w += warps) {
+    const int k = find_domain(pl.bulk, pl.n, w);
+    const DomRec& r = recs[k];
+    bulk_unit<Q, S, COLL>(r.d, r.p, r.parity, w - pl.bulk[k], r.d.counts[5]);
+  }
+}
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(128) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
+  const int total = pl.band[pl.n];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const int k = find_domain(pl.band, pl.n, g);
+    const DomRec& r = recs[k];
+    const int i = g - pl.band[k];
+    if (i >= r.d.counts[r.parity]) continue;
+    bool bad = false;
+    interface_cell<Q, S, COLL>(r.d, r.p, r.parity, i, bad);
+    if (bad) r.d.err[0] = 1;
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kBlock) kb_resolve(const DomRec* __restrict__ recs, BatchPlan pl) {
+  const int total = pl.band[pl.n];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const int k = find_domain(pl.band, pl.n, g);
+    const DomRec& r = recs[k];
+    const int i = g - pl.band[k];
+    if (i < r.d.counts[r.parity]) resolve_cell<Q>(r.d, r.p, r.parity, i);
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kBlock) kb_count(const DomRec* __restrict__ recs, BatchPlan pl) {
+  const int total = pl.band[pl.n];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const int k = find_domain(pl.band, pl.n, g);
+    const DomRec& r = recs[k];
+    const int i = g - pl.band[k];
+    if (i < r.d.counts[r.parity]) count_cell<Q>(r.d, r.p, r.parity, i);
+  }
+}
+
+template <int Q, class S>
+__global__ void __launch_bounds__(128) kb_apply(const DomRec* __restrict__ recs, BatchPlan pl) {
+  const int total = pl.all[pl.n];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const int k = find_domain(pl.all, pl.n, g);
+    const DomRec& r = recs[k];
+    const int i = g - pl.all[k];
+    if (i < r.d.counts[r.parity] + r.d.counts[2]) apply_cell<Q, S>(r.d, r.p, r.parity, i);
+  }
+}
+
+static __global__ void __launch_bounds__(kBlock) kb_finalize(const DomRec* __restrict__ recs, BatchPlan pl) {
+  const int total = pl.all[pl.n];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int base = wid * 32; base < total; base += warps * 32) {
+    const int k = find_domain(pl.all, pl.n, base);
+    const DomRec& r = recs[k];
+    finalize_warp(r.d, r.p, r.parity, base - pl.all[k]);
+  }
+}
+
+// Bubble pressures of every domain (one block each), then the step is done
+// and the domain's buffers swap.
+static __global__ void kb_bubble_end(DomRec* recs) {
+  DomRec& r = recs[blockIdx.x];
+  if (r.p.bubble_model && r.d.nb > 0) bubble_update(r.d, r.p);
+  __syncthreads();
+  if (threadIdx.x == 0) r.parity ^= 1;
 }
 
 }  // namespace fslbm

@@ -37,6 +37,11 @@ class fslbm_params(C.Structure):
                 ("stream", C.c_void_p)]
 
 
+class fslbm_tuning(C.Structure):
+    _fields_ = [("bulk_blocks_per_sm", C.c_int), ("band_blocks_per_sm", C.c_int),
+                ("ms_per_step", C.c_double)]
+
+
 class fslbm_obs(C.Structure):
     _fields_ = [("step", C.c_int64), ("total_mass", C.c_double), ("n_liquid", C.c_int64),
                 ("n_interface", C.c_int64), ("n_gas", C.c_int64), ("n_obstacle", C.c_int64),
@@ -51,7 +56,10 @@ _lock = threading.Lock()
 SYMBOLS = ["fslbm_params_default", "fslbm_create", "fslbm_init", "fslbm_step", "fslbm_sync",
            "fslbm_observables", "fslbm_read_fields", "fslbm_bubbles", "fslbm_set_timing",
            "fslbm_stage_times", "fslbm_save", "fslbm_load", "fslbm_interface_count", "fslbm_work_counts",
-           "fslbm_observables_noalloc", "fslbm_destroy", "fslbm_last_error", "fslbm_version"]
+           "fslbm_observables_noalloc", "fslbm_destroy", "fslbm_last_error", "fslbm_version",
+           "fslbm_batch_create", "fslbm_batch_step", "fslbm_batch_sync", "fslbm_batch_autotune",
+           "fslbm_batch_set_tuning", "fslbm_batch_get_tuning", "fslbm_batch_launches",
+           "fslbm_batch_destroy", "fslbm_batch_last_error"]
 
 
 def load(build_if_missing: bool = True):
@@ -105,6 +113,24 @@ def load(build_if_missing: bool = True):
         lib.fslbm_last_error.restype = C.c_char_p
         lib.fslbm_version.argtypes = []
         lib.fslbm_version.restype = C.c_char_p
+        lib.fslbm_batch_create.argtypes = [C.POINTER(p), i, p, C.POINTER(p)]
+        lib.fslbm_batch_create.restype = i
+        lib.fslbm_batch_step.argtypes = [p, i]
+        lib.fslbm_batch_step.restype = i
+        lib.fslbm_batch_sync.argtypes = [p, C.POINTER(C.c_int)]
+        lib.fslbm_batch_sync.restype = i
+        lib.fslbm_batch_autotune.argtypes = [p, i, C.POINTER(fslbm_tuning)]
+        lib.fslbm_batch_autotune.restype = i
+        lib.fslbm_batch_set_tuning.argtypes = [p, C.POINTER(fslbm_tuning)]
+        lib.fslbm_batch_set_tuning.restype = i
+        lib.fslbm_batch_get_tuning.argtypes = [p, C.POINTER(fslbm_tuning)]
+        lib.fslbm_batch_get_tuning.restype = i
+        lib.fslbm_batch_launches.argtypes = [p, C.POINTER(C.c_int64)]
+        lib.fslbm_batch_launches.restype = i
+        lib.fslbm_batch_destroy.argtypes = [p]
+        lib.fslbm_batch_destroy.restype = None
+        lib.fslbm_batch_last_error.argtypes = [p]
+        lib.fslbm_batch_last_error.restype = C.c_char_p
         _lib = lib
         return lib
 
@@ -248,6 +274,68 @@ class Context:
     def load(self, buf):
         buf = np.ascontiguousarray(buf, np.uint8)
         self._check(self.lib.fslbm_load(self.h, _ptr(buf), buf.size))
+
+
+class Batch:
+    """Several initialized contexts advanced together (wraps ``fslbm_batch``):
+    one launch per phase of the step over all member domains.  The members
+    stay usable on their own (``read``, ``observables``, ``step``)."""
+
+    def __init__(self, members, stream=None):
+        self.lib = load()
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        h = C.c_void_p()
+        st = self.lib.fslbm_batch_create(arr, len(self.members), C.c_void_p(int(stream)) if stream else None,
+                                         C.byref(h))
+        if st != OK:
+            raise FslbmError(st, "fslbm_batch_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            raise FslbmError(st, self.lib.fslbm_batch_last_error(self.h).decode())
+        return st
+
+    def step(self, n=1):
+        self._check(self.lib.fslbm_batch_step(self.h, int(n)))
+
+    def sync(self):
+        out = (C.c_int * len(self.members))()
+        st = self.lib.fslbm_batch_sync(self.h, out)
+        return st, list(out)
+
+    def autotune(self, steps=3):
+        t = fslbm_tuning()
+        self._check(self.lib.fslbm_batch_autotune(self.h, int(steps), C.byref(t)))
+        return {"bulk_blocks_per_sm": t.bulk_blocks_per_sm, "band_blocks_per_sm": t.band_blocks_per_sm,
+                "ms_per_step": t.ms_per_step}
+
+    def set_tuning(self, bulk_blocks_per_sm, band_blocks_per_sm):
+        t = fslbm_tuning(int(bulk_blocks_per_sm), int(band_blocks_per_sm), 0.0)
+        self._check(self.lib.fslbm_batch_set_tuning(self.h, C.byref(t)))
+
+    def tuning(self):
+        t = fslbm_tuning()
+        self._check(self.lib.fslbm_batch_get_tuning(self.h, C.byref(t)))
+        return {"bulk_blocks_per_sm": t.bulk_blocks_per_sm, "band_blocks_per_sm": t.band_blocks_per_sm,
+                "ms_per_step": t.ms_per_step}
+
+    def launches(self):
+        n = C.c_int64(0)
+        self._check(self.lib.fslbm_batch_launches(self.h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fslbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def context_for(sc, precision="FP64", stream=None, **over):
