@@ -353,6 +353,166 @@ def bench_ours(args, ws, rank, local):
     return line
 
 
+# ------------------------------------------------ batched and served runs
+
+def _front_radius(fill, L):
+    """Cylindrical dam break: radius of the wetted floor, sqrt(sum phi / pi)
+    over the bottom layer."""
+    return float(np.sqrt(fill.reshape(L, L, L)[0].sum() / np.pi))
+
+
+def _crown(fill, flags, L):
+    """Drop impact: height of the highest interface cell, k + phi."""
+    from paper_2207_13962_gb300 import scenarios as S
+    f3 = fill.reshape(L, L, L)
+    k = np.nonzero((flags.reshape(L, L, L) == S.IFACE).any(axis=(1, 2)))[0]
+    if k.size == 0:
+        return 0.0
+    top = int(k.max())
+    return float(top + f3[top][flags.reshape(L, L, L)[top] == S.IFACE].max())
+
+
+def bench_batch(args):
+    """64 cylindrical dam breaks of seeded uneven sizes (D3Q27 TRT): as one
+    batch in FP32 and in reduced precision, and one at a time in plain FP32.
+    Every run is brought to the same step count, so the front radii compare
+    at the same time."""
+    import torch
+    from paper_2207_13962_gb300 import fslbm
+    from paper_2207_13962_gb300 import scenarios as S
+    torch.cuda.set_device(0)
+    prm = S.cylinder_batch_params(n=args.batch_n)
+    scs = [S.cylinder_dam_break(**p, q=27) for p in prm]
+    cells = sum(sc.N for sc in scs)
+    steps = args.batch_steps
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    def observe(ctxs):
+        return [(_front_radius(c.read(pdf=False)["fill"], sc.shape[0]), c.observables()["total_mass"])
+                for sc, c in zip(scs, ctxs)]
+
+    res, obs_at, total = {}, {}, None
+    for prec in ("FP32", args.batch_precision):
+        ctxs = [fslbm.context_for(sc, precision=prec, stream=stream.cuda_stream) for sc in scs]
+        m0 = [c.observables()["total_mass"] for c in ctxs]
+        batch = fslbm.Batch(ctxs, stream=stream.cuda_stream)
+        tune = batch.autotune(steps=1) if args.autotune else batch.tuning()
+        done = ctxs[0].observables()["step"]
+        if total is None:
+            total = max(done, args.warmup) + steps
+        batch.step(total - steps - done)
+        t = timed(lambda: batch.step(steps))
+        obs_at[prec] = observe(ctxs)
+        res[f"batched_{prec.lower()}"] = {
+            "mlups": cells * steps / t / 1e6, "seconds": t, "tuning": tune, "launches": batch.launches(),
+            "mass_drift_rel_max": max(abs(o[1] - m) / m for o, m in zip(obs_at[prec], m0))}
+        batch.close()
+        for c in ctxs:
+            c.close()
+    # plain: each domain alone, one after another, FP32
+    ctxs = [fslbm.context_for(sc, precision="FP32", stream=stream.cuda_stream) for sc in scs]
+    m0 = [c.observables()["total_mass"] for c in ctxs]
+    for c in ctxs:
+        c.step(total - steps)
+    t = timed(lambda: [c.step(steps) for c in ctxs])
+    ref = observe(ctxs)
+    res["plain_fp32"] = {"mlups": cells * steps / t / 1e6, "seconds": t,
+                         "mass_drift_rel_max": max(abs(o[1] - m) / m for o, m in zip(ref, m0))}
+    for c in ctxs:
+        c.close()
+    for prec, obs in obs_at.items():
+        res[f"batched_{prec.lower()}"]["front_radius_rel_err_vs_plain_fp32"] = max(
+            abs(a[0] - b[0]) / max(b[0], 1e-30) for a, b in zip(obs, ref))
+    line = {"metric": METRIC, "workload": "batched cylindrical dam breaks",
+            "config": {"domains": len(scs), "cells": cells, "lattice": "D3Q27", "collision": "TRT",
+                       "sides": [p["L"] for p in prm], "timed_steps": steps, "steps_total": total,
+                       "seed": 2207, "g": 1e-5, "nu": 1e-3, "variant": "OM"},
+            "unit": "MLUPS", "results": res, "data": "synthetic (seeded generator, no dataset)"}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def bench_serve(args):
+    """Drop impacts arriving as a Poisson stream (mean 20 req/s, seeded sizes
+    96..256): a FIFO one-at-a-time plain FP32 server (simulated on the
+    measured run times) against the continuous-batching server in FP32 and
+    in reduced precision, replayed in real time."""
+    import torch
+    from paper_2207_13962_gb300 import fslbm
+    from paper_2207_13962_gb300 import scenarios as S
+    torch.cuda.set_device(0)
+    trace = S.drop_requests(n=args.requests)
+    scs = [(t, S.drop_impact(**kw)) for t, kw in trace]
+    steps = args.serve_steps
+    cells = sum(sc.N for _, sc in scs)
+    out = {}
+    # plain: each request alone in arrival order; time-to-result includes
+    # the wait behind earlier requests (FIFO, one at a time)
+    run_s, ref = [], []
+    for _, sc in scs:
+        c = fslbm.context_for(sc, precision="FP32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.step(steps)
+        c.sync()
+        run_s.append(time.perf_counter() - t0)
+        r = c.read(pdf=False)
+        ref.append((_crown(r["fill"], r["flags"], sc.shape[0]), c.observables()["total_mass"]))
+        c.close()
+    clock, ttr = 0.0, []
+    for (arr, _), rs in zip(scs, run_s):
+        clock = max(clock, arr) + rs
+        ttr.append(clock - arr)
+    out["plain_fp32_fifo"] = {"mlups": cells * steps / sum(run_s) / 1e6, "busy_seconds": sum(run_s),
+                              "p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
+                              "makespan_s": clock}
+    for prec in ("FP32", args.batch_precision):
+        srv = fslbm.Server(q=19, precision=prec, max_active=args.max_active, chunk_steps=args.chunk_steps)
+        pending = list(range(len(scs)))
+        ids, results = {}, {}
+        t0 = time.perf_counter()
+        while len(results) < len(scs):
+            now = time.perf_counter() - t0
+            while pending and scs[pending[0]][0] <= now:
+                k = pending.pop(0)
+                ids[srv.submit(scs[k][1], steps)] = k
+            if srv.stats()["active"] == 0 and srv.stats()["queued"] == 0 and pending:
+                time.sleep(max(0.0, scs[pending[0]][0] - (time.perf_counter() - t0)))
+                continue
+            srv.poll()
+            for rid, k in list(ids.items()):
+                r = srv.result(rid)
+                if r is not None:
+                    results[k] = r
+                    del ids[rid]
+        makespan = time.perf_counter() - t0
+        ttr = [results[k]["t_result"] for k in range(len(scs))]
+        err = max(abs(_crown(results[k]["fill"], results[k]["flags"], scs[k][1].shape[0]) - ref[k][0]) /
+                  max(ref[k][0], 1e-30) for k in range(len(scs)))
+        st = srv.stats()
+        out[f"served_{prec.lower()}"] = {"mlups": cells * steps / makespan / 1e6, "makespan_s": makespan,
+                                         "p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
+                                         "crown_rel_err_vs_plain_fp32": err, "max_active_seen": st["max_active_seen"],
+                                         "batch_rebuilds": st["batch_rebuilds"]}
+        srv.close()
+    line = {"metric": METRIC, "workload": "served drop impacts (continuous batching)",
+            "config": {"requests": len(scs), "cells": cells, "steps_per_request": steps, "rate_per_s": 20.0,
+                       "seed": 13962, "sides": [sc.shape[0] for _, sc in scs], "max_active": args.max_active,
+                       "chunk_steps": args.chunk_steps, "lattice": "D3Q19", "collision": "TRT", "variant": "OM"},
+            "unit": "MLUPS", "results": out, "data": "synthetic (seeded generator, no dataset)"}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 # --------------------------------------------------------- reference arm
 
 def bench_reference(args, ws, rank):
@@ -394,15 +554,30 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "taylor_bubble_256", "dam_break", "box512"])
+    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "taylor_bubble_256", "dam_break", "box512",
+                                                       "batch_cylinders", "serve_drops"])
     ap.add_argument("--precision", default="FP32", choices=list(S_BYTES))
     ap.add_argument("--variant", default="OM", choices=["NBRC", "NBKC", "OM", "OM3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=64, help="batch_cylinders: domains")
+    ap.add_argument("--batch-steps", type=int, default=200, help="batch_cylinders: timed steps")
+    ap.add_argument("--batch-precision", default="FP16S", choices=["FP16S", "BF16S", "FP32"])
+    ap.add_argument("--autotune", action="store_true", help="batch_cylinders: autotune the launch shape")
+    ap.add_argument("--requests", type=int, default=24, help="serve_drops: requests of the trace")
+    ap.add_argument("--serve-steps", type=int, default=1000, help="serve_drops: steps per request")
+    ap.add_argument("--max-active", type=int, default=16, help="serve_drops: resident runs")
+    ap.add_argument("--chunk-steps", type=int, default=100, help="serve_drops: steps per round")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     ws, rank, local = dist_env()
+    if args.workload == "batch_cylinders" and args.impl == "ours":
+        bench_batch(args)
+        return
+    if args.workload == "serve_drops" and args.impl == "ours":
+        bench_serve(args)
+        return
     if args.impl == "reference":
         bench_reference(args, ws, rank)
         return

@@ -209,8 +209,10 @@ const char* fslbm_version(void);
  * Many domains of different sizes advance together: each phase of the step
  * (geometry, bulk stream-collide, interface update, conversion, excess mass,
  * bubbles; Sec. 2.2, 3) runs as ONE launch over a block table of all member
- * domains, captured once in a CUDA graph.  Results are the same as stepping
- * each member alone (same kernels, bitwise).
+ * domains, captured once in a CUDA graph.  Results are those of stepping
+ * each member alone: bitwise in FP64 (compiled without multiply-add
+ * contraction), to FP32 rounding otherwise (the compiler may contract the
+ * shared per-cell code differently in the batched kernels).
  *
  * Members are initialized contexts of the same lattice, precision and
  * collision operator (variant, omega, g, sigma, eps_phi, bubble model and
@@ -255,6 +257,81 @@ fslbm_status fslbm_batch_get_tuning(const fslbm_batch* b, fslbm_tuning* t);
 fslbm_status fslbm_batch_launches(const fslbm_batch* b, int64_t* n);
 void fslbm_batch_destroy(fslbm_batch* b);
 const char* fslbm_batch_last_error(const fslbm_batch* b);
+
+/* Device bytes a context of this domain holds, including the peak of
+ * fslbm_init's staging buffers (with_velocity: a velocity field is passed).
+ * FSLBM_EINVAL for bad sizes or enums. */
+fslbm_status fslbm_memory_estimate(const fslbm_domain* domain, fslbm_lattice lattice, int precision,
+                                   int with_velocity, size_t* bytes);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop with continuous batching.  Runs of different domain sizes
+ * are submitted as they arrive; each poll admits queued runs in arrival
+ * order while slots (max_active) and device memory (memory_budget, by
+ * fslbm_memory_estimate) allow, keeps the admitted runs' PDFs, flags and
+ * fill levels resident, advances all of them together by up to chunk_steps
+ * steps in the shared launches of one batch (rebuilt when the membership
+ * changes), and retires the runs that are done: their fill levels, flags and
+ * observables are copied to the host and their device memory is freed for
+ * the next admissions.  A run's result is that of running it alone (bitwise
+ * in FP64, to FP32 rounding otherwise; see batches). */
+typedef struct fslbm_server fslbm_server;
+
+typedef struct {
+  fslbm_lattice lattice;     /* shared by all runs */
+  fslbm_collision collision; /* shared by all runs */
+  int precision;             /* fslbm_precision, shared by all runs */
+  int max_active;            /* resident runs at most (>= 1) */
+  int chunk_steps;           /* steps between admission rounds (>= 1) */
+  int64_t memory_budget;     /* device bytes for resident runs; 0: 90 % of
+                                the memory free when the server is created */
+  void* stream;              /* cudaStream_t for all work, NULL = default */
+} fslbm_server_config;
+
+typedef struct {
+  fslbm_domain domain;
+  fslbm_bc_variant bc_variant;
+  fslbm_params params;       /* precision must equal the server's; stream ignored */
+  const double* fill;        /* host arrays as for fslbm_init, copied at submit */
+  const uint8_t* flags;
+  const double* velocity;    /* may be NULL */
+  const double* density;     /* may be NULL */
+  int steps;                 /* steps to run */
+} fslbm_request;
+
+typedef struct {
+  int64_t id;
+  int status;                /* fslbm_status of the run (init or final state) */
+  int64_t steps;             /* steps done */
+  int64_t cells;
+  fslbm_obs obs;             /* observables of the final state */
+  double t_queue;            /* seconds from submit to admission */
+  double t_result;           /* seconds from submit to the result (time-to-result) */
+} fslbm_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed;
+  int queued, active, max_active_seen;
+  int64_t batch_rebuilds, batch_steps;
+  double cell_updates;       /* cells x steps of the completed runs */
+  int64_t memory_used, memory_budget;
+} fslbm_server_stats;
+
+fslbm_status fslbm_server_create(const fslbm_server_config* cfg, fslbm_server** out);
+/* Queue a run (host arrays copied); *id identifies its result.  FSLBM_ENOMEM
+ * if the run alone exceeds the memory budget. */
+fslbm_status fslbm_server_submit(fslbm_server* s, const fslbm_request* rq, int64_t* id);
+/* One round: admit, step the resident runs by up to chunk_steps (synchronous),
+ * retire finished runs.  *n_active (may be NULL): runs resident afterwards. */
+fslbm_status fslbm_server_poll(fslbm_server* s, int* n_active);
+/* Result of a finished run (FSLBM_ESTATE while it is not finished); fill[N]
+ * and flags[N] (may be NULL) receive its final fields.  The result is
+ * released by this call. */
+fslbm_status fslbm_server_result(fslbm_server* s, int64_t id, fslbm_result* res, double* fill,
+                                 uint8_t* flags);
+fslbm_status fslbm_server_stats_get(const fslbm_server* s, fslbm_server_stats* out);
+void fslbm_server_destroy(fslbm_server* s);
+const char* fslbm_server_last_error(const fslbm_server* s);
 
 #ifdef __cplusplus
 }

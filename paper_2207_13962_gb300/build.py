@@ -25,6 +25,7 @@ SOURCES = {
     "fslbm_f16.cu": [],
     "fslbm_noalloc.cu": [],
     "fslbm_batch.cu": [],
+    "fslbm_server.cu": [],
 }
 
 

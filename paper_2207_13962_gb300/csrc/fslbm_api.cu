@@ -124,60 +124,6 @@ int launches_per_step(const fslbm_ctx* c) {
   return 7 + ((c->kp.bubble_model && c->d.nb > 0) ? 1 : 0);
 }
 
-// Host labelling of connected gas regions in the order of their lowest cell
-// index (lattice neighbourhood, periodic wrap); interface cells take the
-// lowest label of their gas neighbours.
-void label_bubbles(const fslbm_ctx* c, const uint8_t* flags, std::vector<int>& bid, int& nb) {
-  const int nx = c->dom.nx, ny = c->dom.ny, nz = c->dom.nz;
-  const long long N = (long long)nx * ny * nz;
-  bid.assign((size_t)N, -1);
-  std::vector<int> stack;
-  auto nbr = [&](int x, int y, int z, int dx, int dy, int dz) -> long long {
-    int X = x + dx, Y = y + dy, Z = z + dz;
-    if (X < 0 || X >= nx) {
-      if (!c->dom.periodic[0]) return -1;
-      X = (X % nx + nx) % nx;
-    }
-    if (Y < 0 || Y >= ny) {
-      if (!c->dom.periodic[1]) return -1;
-      Y = (Y % ny + ny) % ny;
-    }
-    if (Z < 0 || Z >= nz) {
-      if (!c->dom.periodic[2]) return -1;
-      Z = (Z % nz + nz) % nz;
-    }
-    return (long long)X + (long long)nx * (Y + (long long)ny * Z);
-  };
-  nb = 0;
-  for (long long s = 0; s < N; ++s) {
-    if (flags[s] != T_GAS || bid[s] >= 0) continue;
-    bid[s] = nb;
-    stack.push_back((int)s);
-    while (!stack.empty()) {
-      const int a = stack.back();
-      stack.pop_back();
-      const int x = a % nx, y = (a / nx) % ny, z = a / (nx * ny);
-      for (int i = 1; i < c->q; ++i) {
-        const long long n = nbr(x, y, z, CX(i), CY(i), CZ(i));
-        if (n >= 0 && flags[n] == T_GAS && bid[n] < 0) {
-          bid[n] = nb;
-          stack.push_back((int)n);
-        }
-      }
-    }
-    ++nb;
-  }
-  for (long long s = 0; s < N; ++s) {
-    if (flags[s] != T_IFACE) continue;
-    const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
-    int best = -1;
-    for (int i = 1; i < c->q; ++i) {
-      const long long n = nbr(x, y, z, CX(i), CY(i), CZ(i));
-      if (n >= 0 && flags[n] == T_GAS && (best < 0 || bid[n] < best)) best = bid[n];
-    }
-    bid[s] = best;
-  }
-}
 
 bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
 
@@ -267,7 +213,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   c->band_grid = sms * 2;
   // the persistent bulk sweep leaves FSLBM_BULK_RESERVE block slots per SM to
   // the interface-band kernels that run beside it
-  c->bulk_grid = sms * ((params->precision == FSLBM_FP64 ? 2 : kBulkMinBlocks32) - FSLBM_BULK_RESERVE);
+  c->bulk_grid = sms * (c->ops.bulk_blocks_per_sm - FSLBM_BULK_RESERVE) * FSLBM_BULK_WAVES;
 
   DPtrs& d = c->d;
   std::memset(&d, 0, sizeof(d));
@@ -326,6 +272,31 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
     return s;
   }
   *out = c;
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_memory_estimate(const fslbm_domain* domain, fslbm_lattice lattice, int precision,
+                                   int with_velocity, size_t* bytes) {
+  if (!domain || !bytes || domain->nx < 1 || domain->ny < 1 || domain->nz < 1) return FSLBM_EINVAL;
+  if (lattice != FSLBM_D3Q19 && lattice != FSLBM_D3Q27) return FSLBM_EINVAL;
+  if (precision < FSLBM_FP64 || precision > FSLBM_BF16S) return FSLBM_EINVAL;
+  const double Nd = (double)domain->nx * domain->ny * domain->nz;
+  if (Nd > 2147483647.0) return FSLBM_EINVAL;
+  const size_t N = (size_t)Nd;
+  const size_t Np = (N + 63) / 64 * 64;
+  const size_t elem = precision == FSLBM_FP64 ? 8 : precision == FSLBM_FP32 ? 4 : 2;
+  const size_t rs = precision == FSLBM_FP64 ? 8 : 4;
+  const size_t n4 = (N + 3) / 4 * 4;
+  const size_t ntiles =
+      (size_t)((domain->nx + 7) / 8) * ((domain->ny + 7) / 8) * ((domain->nz + 7) / 8);
+  const size_t nseg = (N + kSegCells - 1) / kSegCells;
+  size_t b = 2 * (size_t)lattice * Np * elem;            // PDFs, two buffers
+  b += 6 * n4;                                           // flags, cls, mark, conv, cfin, claim
+  b += N * (4 + 8 + 8 + 4 + 8 + 4 + 4 + 4);              // wallmask phi mass bid share band[2] newlist
+  b += N * (4 * rs + 3 * 8);                             // nhat rhog m_next phi_next rho_band
+  b += 3 * ntiles * 4 + 2 * nseg * 4 + 4096;             // tiles, segments, counters, partials
+  b += N * (1 + 8 + 8) + (with_velocity ? 24 * N : 0);   // fslbm_init staging (peak)
+  *bytes = b;
   return FSLBM_OK;
 }
 
@@ -390,28 +361,8 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
                 (hbad & 2) ? "a liquid cell touches a gas cell (interface layer not closed)"
                            : "flag value > 3");
   }
-  // bubbles (host labelling, fixed-point initial volumes)
-  std::vector<int> bid;
-  int nb = 0;
-  std::vector<double> V0;
-  std::vector<long long> gas;
-  if (c->kp.bubble_model) {
-    label_bubbles(c, flags, bid, nb);
-    std::vector<long long> acc((size_t)(nb > 0 ? nb : 1), 0);
-    gas.assign((size_t)(nb > 0 ? nb : 1), 0);
-    for (size_t s = 0; s < N; ++s) {
-      const int b = bid[s];
-      if (b < 0) continue;
-      if (flags[s] == T_GAS) {
-        acc[b] += 4294967296LL;
-        gas[b] += 1;
-      } else if (flags[s] == T_IFACE) {
-        acc[b] += (long long)llrint((1.0 - fill[s]) * 4294967296.0);
-      }
-    }
-    V0.resize((size_t)(nb > 0 ? nb : 1));
-    for (int b = 0; b < nb; ++b) V0[b] = (double)acc[b] / 4294967296.0;
-  }
+  // bubbles: connected gas regions labelled on the device, fixed-point
+  // initial volumes
   DPtrs& d = c->d;
   dfree(c, d.V0);
   dfree(c, d.pV);
@@ -420,6 +371,32 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   dfree(c, d.Vcur);
   d.V0 = d.pV = d.Vcur = nullptr;
   d.gas_cnt = d.iface_fix = nullptr;
+  int nb = 0;
+  const int gcells = (c->kp.N + kBlock - 1) / kBlock;
+  if (c->kp.bubble_model) {
+    const int nchunks = (c->kp.N + kCcChunk - 1) / kCcChunk;
+    int* lab = d.band[1];      // free until the first step
+    int* root_id = d.newlist;  // free until the first step
+    int *cnt = nullptr, *off = nullptr;
+    if (e == cudaSuccess) e = dalloc(c, &cnt, (size_t)nchunks * sizeof(int));
+    if (e == cudaSuccess) e = dalloc(c, &off, (size_t)(nchunks + 1) * sizeof(int));
+    if (e == cudaSuccess) {
+      k_cc_init<<<gcells, kBlock, 0, st>>>(raw, c->kp.N, lab);
+      c->ops.cc_union(raw, c->kp, lab, st);
+      k_cc_compress<<<gcells, kBlock, 0, st>>>(c->kp.N, lab);
+      k_cc_count<<<nchunks, kBlock, 0, st>>>(c->kp.N, lab, cnt);
+      k_cc_scan<<<1, 1024, 0, st>>>(nchunks, cnt, off);
+      k_cc_number<<<nchunks, 32, 0, st>>>(c->kp.N, lab, off, root_id);
+      c->ops.cc_assign(raw, c->kp, lab, root_id, d.bid, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, off + nchunks, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(c, cnt);
+    dfree(c, off);
+  } else if (e == cudaSuccess) {
+    e = cudaMemsetAsync(d.bid, 0xff, N * sizeof(int), st);
+  }
   d.nb = nb;
   const size_t nbb = (size_t)(nb > 0 ? nb : 1);
   if (e == cudaSuccess) e = dalloc(c, &d.V0, nbb * sizeof(double));
@@ -427,22 +404,21 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   if (e == cudaSuccess) e = dalloc(c, &d.gas_cnt, nbb * sizeof(long long));
   if (e == cudaSuccess) e = dalloc(c, &d.iface_fix, nbb * sizeof(long long));
   if (e == cudaSuccess) e = dalloc(c, &d.Vcur, nbb * sizeof(double));
-  if (e == cudaSuccess) {
-    std::vector<double> pv(nbb, c->kp.pv0);
-    if (nb > 0) {
-      e = cudaMemcpy(d.V0, V0.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(d.Vcur, V0.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(d.pV, pv.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(d.gas_cnt, gas.data(), nb * sizeof(long long), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemset(d.iface_fix, 0, nb * sizeof(long long));
+  if (e == cudaSuccess && nb > 0) {
+    e = cudaMemsetAsync(d.gas_cnt, 0, nbb * sizeof(long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.iface_fix, 0, nbb * sizeof(long long), st);
+    if (e == cudaSuccess) {
+      k_cc_volumes<<<gcells, kBlock, 0, st>>>(raw, dfill, c->kp.N, d.bid, d.gas_cnt, d.iface_fix);
+      k_cc_v0<<<(nb + 255) / 256, 256, 0, st>>>(nb, d.gas_cnt, d.iface_fix, d.V0, d.Vcur, d.pV,
+                                                 c->kp.pv0);
+      e = cudaGetLastError();
     }
   }
-  if (e == cudaSuccess) {
-    if (c->kp.bubble_model)
-      e = cudaMemcpyAsync(d.bid, bid.data(), N * sizeof(int), cudaMemcpyHostToDevice, st);
-    else
-      e = cudaMemsetAsync(d.bid, 0xff, N * sizeof(int), st);
-  }
+  // clear both PDF buffers: gas and obstacle slots hold no PDFs of their
+  // own (obstacle slots receive reflected copies from their neighbours)
+  const size_t pdf_bytes = (size_t)c->q * (size_t)c->kp.Np * c->ops.elem_size;
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.pdf[0], 0, pdf_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.pdf[1], 0, pdf_bytes, st);
   if (e == cudaSuccess) {
     c->ops.init_cells(d, c->kp, raw, dfill, dvel, dden, st);
     e = cudaGetLastError();

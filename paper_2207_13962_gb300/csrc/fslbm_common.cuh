@@ -13,11 +13,12 @@
 namespace fslbm {
 
 // ----------------------------------------------------------------- flags
-// bits 0-1: cell type; bit 2: static "a lattice neighbour is an obstacle or
-// lies outside a non-periodic face"; bit 3: static "a lattice neighbour lies
-// across a periodic face" (both computed once at init).
+// bits 0-1: cell type; static bits (computed once at init): bit 2 "a lattice
+// neighbour is an obstacle cell", bit 3 "a lattice neighbour lies across a
+// periodic face", bit 4 "a lattice neighbour lies outside a non-periodic
+// face".
 enum : uint8_t { T_GAS = 0, T_IFACE = 1, T_LIQ = 2, T_OBST = 3 };
-enum : uint8_t { F_TYPE = 3, F_NEAR_WALL = 4, F_WRAP = 8 };
+enum : uint8_t { F_TYPE = 3, F_NEAR_WALL = 4, F_WRAP = 8, F_FACE = 16 };
 // Thuerey classes of interface cells.
 enum : uint8_t { CL_STD = 0, CL_NF = 1, CL_NE = 2 };
 // Conversion marks.
@@ -185,7 +186,8 @@ struct DPtrs {
   void* pdf[2];
   uint8_t* flags;
   uint32_t* wallmask;  // bit i: the pull source of direction i is an obstacle
-                       // or outside a non-periodic face (static)
+                       // cell (static); sources outside the domain are not
+                       // included
   double* phi;
   double* mass;
   int* bid;

@@ -10,6 +10,10 @@ namespace fslbm {
 
 template <int Q, class S>
 struct Engine {
+  // persistent bulk blocks per SM the sweep is compiled for
+  static constexpr int bulk_blocks_per_sm() {
+    return sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2;
+  }
   static int grid_cells(const KParams& p) { return (p.N + kBlock - 1) / kBlock; }
 
   static void init_cells(const DPtrs& d, const KParams& p, const uint8_t* raw, const double* fill,
@@ -18,6 +22,13 @@ struct Engine {
   }
   static void init_check(const KParams& p, const uint8_t* raw, int* bad, cudaStream_t st) {
     k_init_check<Q><<<grid_cells(p), kBlock, 0, st>>>(raw, p, bad);
+  }
+  static void cc_union(const uint8_t* raw, const KParams& p, int* lab, cudaStream_t st) {
+    k_cc_union<Q><<<grid_cells(p), kBlock, 0, st>>>(raw, p, lab);
+  }
+  static void cc_assign(const uint8_t* raw, const KParams& p, const int* lab, const int* root_id,
+                        int* bid, cudaStream_t st) {
+    k_cc_assign<Q><<<grid_cells(p), kBlock, 0, st>>>(raw, p, lab, root_id, bid);
   }
 
   // One step reading pdf[parity], band[parity]; writing the other buffers.
@@ -41,7 +52,7 @@ struct Engine {
       bulk(fk->side);
       cudaEventRecord(fk->join, fk->side);
     }
-    k_geometry<Q, S><<<band_grid, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(d, p, parity);
+    k_geometry<Q, S><<<band_grid * kGeoGridMult, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(d, p, parity);
     if (ev) ev->mark(1, st);
     if (!forked) bulk(st);
     if (ev) ev->mark(2, st);
@@ -73,7 +84,7 @@ struct Engine {
     else
       kb_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, fk->side>>>(recs, pl);
     cudaEventRecord(fk->join, fk->side);
-    kb_geometry<Q, S><<<band_grid, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(recs, pl);
+    kb_geometry<Q, S><<<band_grid * kGeoGridMult, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(recs, pl);
     if (collision == 0)
       kb_interface<Q, S, 0><<<band_grid * 2, 128, 0, st>>>(recs, pl);
     else
@@ -105,6 +116,8 @@ struct Engine {
     Ops o;
     o.init_cells = &init_cells;
     o.init_check = &init_check;
+    o.cc_union = &cc_union;
+    o.cc_assign = &cc_assign;
     o.step = &step;
     o.observables = &observables;
     o.pdf_out = &pdf_out;
@@ -112,6 +125,7 @@ struct Engine {
     o.real_size = sizeof(typename S::Real);
     o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
     o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
+    o.bulk_blocks_per_sm = bulk_blocks_per_sm();
     o.batch_step = &batch_step;
     o.batch_bulk_fn[0] = (const void*)&kb_bulk<Q, S, 0>;
     o.batch_bulk_fn[1] = (const void*)&kb_bulk<Q, S, 1>;

@@ -28,6 +28,10 @@ struct Ops {
   void (*init_cells)(const DPtrs&, const KParams&, const uint8_t* raw, const double* fill,
                      const double* vel, const double* den, cudaStream_t);
   void (*init_check)(const KParams&, const uint8_t* raw, int* bad, cudaStream_t);
+  // bubble labelling at init: unions of neighbouring gas cells, ids of cells
+  void (*cc_union)(const uint8_t* raw, const KParams&, int* lab, cudaStream_t);
+  void (*cc_assign)(const uint8_t* raw, const KParams&, const int* lab, const int* root_id,
+                    int* bid, cudaStream_t);
   void (*step)(const DPtrs&, const KParams&, int parity, int band_grid, int bulk_grid,
                cudaStream_t, StageEvents*, const Fork*);
   void (*observables)(const DPtrs&, const KParams&, int parity, double* out, cudaStream_t);
@@ -36,6 +40,7 @@ struct Ops {
   size_t real_size;
   const void* bulk_fn[2];  // the bulk sweep kernels (SRT, TRT): graph nodes of
                            // every other kernel get the higher priority
+  int bulk_blocks_per_sm;  // resident blocks per SM of the persistent bulk sweep
   // one step of every domain of a block table (see DomRec, BatchPlan)
   void (*batch_step)(DomRec* recs, const BatchPlan& plan, int band_grid, int bulk_grid,
                      int collision, cudaStream_t, const Fork*);

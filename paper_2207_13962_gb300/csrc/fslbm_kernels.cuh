@@ -65,6 +65,43 @@ __device__ __forceinline__ int warp_append(int* counter, bool pred) {
   return pred ? base + __popc(b & ((1u << lane) - 1u)) : -1;
 }
 
+// Block-wide exclusive prefix sum (one block) of values f(k), k < n, into
+// off[0..n]; f must not read off.
+template <class F>
+__device__ __forceinline__ void block_prefix(int n, int* off, F f) {
+  __shared__ int carry;
+  __shared__ int wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    const int v = k < n ? f(k) : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = lane < nw ? wsum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wsum[lane] = t;
+    }
+    __syncthreads();
+    const int incl = x + (wid > 0 ? wsum[wid - 1] : 0) + carry;
+    if (k < n) off[k + 1] = incl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[0] = 0;
+}
+
 // ---------------------------------------------------------- cell algebra
 // Eq. nm-lbm-equilibrium with c_s^2 = 1/3.
 template <int Q, class R>
@@ -277,6 +314,46 @@ __device__ __forceinline__ void post_moments(const typename S::T* P, long long N
   u[2] = jz / rr - R(0.5) * R(p.g[2]);
 }
 
+// ------------------------------------------------- bounce-back via obstacle slots
+// Slice-i index of the pull source of direction i of cell c at (x, y, z):
+// the neighbour x - c_i, wrapped across periodic faces, or the cell's own
+// slot ibar (bounce-back) when the source lies outside a non-periodic face.
+template <int Q>
+__device__ __forceinline__ long long pull_index_general(const KParams& p, int c, int x, int y,
+                                                        int z, int i) {
+  int X = x - CX(i), Y = y - CY(i), Z = z - CZ(i);
+  bool out = false;
+  if (X < 0 || X >= p.nx) {
+    if (p.per[0]) X = X < 0 ? X + p.nx : X - p.nx;
+    else out = true;
+  }
+  if (Y < 0 || Y >= p.ny) {
+    if (p.per[1]) Y = Y < 0 ? Y + p.ny : Y - p.ny;
+    else out = true;
+  }
+  if (Z < 0 || Z >= p.nz) {
+    if (p.per[2]) Z = Z < 0 ? Z + p.nz : Z - p.nz;
+    else out = true;
+  }
+  return out ? (long long)OPP(i) * p.Np + c : (long long)i * p.Np + (X + p.nx * (Y + p.ny * Z));
+}
+
+// Reflected copies of a fluid cell's post-collision PDFs (working
+// representation f) into the slots of its obstacle pull sources.
+template <int Q, class S>
+__device__ __forceinline__ void write_reflected(const DPtrs& d, const KParams& p, typename S::T* B,
+                                                int c, uint32_t wm, bool general,
+                                                const typename S::Real* f) {
+  int x = 0, y = 0, z = 0;
+  if (general) decode(p, c, x, y, z);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (!((wm >> i) & 1u)) continue;
+    const long long idx = general ? pull_index_general<Q>(p, c, x, y, z, i) : p.dofs[i] + c;
+    B[idx] = store_w<S, Q>(f[OPP(i)], i);
+  }
+}
+
 // ------------------------------------------------------------------ init
 // Validates raw flags: values <= 3 and no liquid cell next to a gas cell.
 template <int Q>
@@ -314,11 +391,12 @@ __global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __re
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     int n = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-    if (n < 0 || raw[n] == T_OBST) fl |= F_NEAR_WALL;
+    if (n < 0) fl |= F_FACE;
+    else if (raw[n] == T_OBST) fl |= F_NEAR_WALL;
     const int X = x + CX(i), Y = y + CY(i), Z = z + CZ(i);
     if (n >= 0 && (X < 0 || X >= p.nx || Y < 0 || Y >= p.ny || Z < 0 || Z >= p.nz)) fl |= F_WRAP;
     const int s = nbr(p, x, y, z, -CX(i), -CY(i), -CZ(i));
-    if (s < 0 || raw[s] == T_OBST) wm |= 1u << i;
+    if (s >= 0 && raw[s] == T_OBST) wm |= 1u << i;
   }
   d.flags[c] = fl;
   d.wallmask[c] = wm;
@@ -334,27 +412,31 @@ __global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __re
   typename S::T* P = (typename S::T*)d.pdf[parity];
   typename S::T* P2 = (typename S::T*)d.pdf[parity ^ 1];
   const bool fluid = (t == T_LIQ || t == T_IFACE);
+  if (!fluid) return;  // gas and obstacle slots stay as cleared (obstacle
+                       // slots receive their neighbours' reflected copies)
+  R fe[Q];
   if constexpr (S::kDev) {
     // deviation f^eq - w formed in FP64, rounded once to the stored format
     const double ux = vel ? vel[c] : 0.0;
     const double uy = vel ? vel[(long long)p.N + c] : 0.0;
     const double uz = vel ? vel[2LL * p.N + c] : 0.0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const double de = fluid ? feq_dev<Q, double>(i, r - 1.0, r, ux, uy, uz) : -W<Q, double>(i);
-      P[(long long)i * p.Np + c] = S::stored(float(de));
-      P2[(long long)i * p.Np + c] = S::stored(float(de));
-    }
+    for (int i = 0; i < Q; ++i) fe[i] = R(feq_dev<Q, double>(i, r - 1.0, r, ux, uy, uz));
   } else {
     const R ux = vel ? R(vel[c]) : R(0.0);
     const R uy = vel ? R(vel[(long long)p.N + c]) : R(0.0);
     const R uz = vel ? R(vel[2LL * p.N + c]) : R(0.0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      R fe = fluid ? feq_i<Q, R>(i, R(r), ux, uy, uz) : R(0.0);
-      P[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
-      P2[(long long)i * p.Np + c] = S::store(fe, W<Q, R>(i));
-    }
+    for (int i = 0; i < Q; ++i) fe[i] = feq_i<Q, R>(i, R(r), ux, uy, uz);
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    P[(long long)i * p.Np + c] = store_w<S, Q>(fe[i], i);
+    P2[(long long)i * p.Np + c] = store_w<S, Q>(fe[i], i);
+  }
+  if (wm) {
+    write_reflected<Q, S>(d, p, P, c, wm, (fl & F_WRAP) != 0, fe);
+    write_reflected<Q, S>(d, p, P2, c, wm, (fl & F_WRAP) != 0, fe);
   }
 }
 
@@ -365,6 +447,169 @@ static __global__ void k_compact_full(const uint8_t* __restrict__ flags, int N, 
   bool pred = (c < N) && ((flags[c] & F_TYPE) == T_IFACE);
   int pos = warp_append(count, pred);
   if (pred) list[pos] = c;
+}
+
+// -------------------------------------------------------- bubble labels
+// Connected gas regions (lattice neighbourhood, periodic wrap) at init, on
+// the device.  Union-find with lock-free hooking: every gas cell starts as
+// its own root; a union hooks the larger of two roots under the smaller one
+// with compare-and-swap (a root is re-parented only while it is still a
+// root), so labels only decrease and every root ends as the lowest cell
+// index of its component.  Bubbles are then numbered in the order of their
+// roots, i.e. of their lowest cell index.
+__device__ __forceinline__ int cc_find(const int* lab, int x) {
+  int p = lab[x];
+  while (p != x) {
+    x = p;
+    p = lab[x];
+  }
+  return x;
+}
+
+static __global__ void k_cc_init(const uint8_t* __restrict__ raw, int N, int* lab) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) lab[c] = raw[c] == T_GAS ? c : -1;
+}
+
+template <int Q>
+__global__ void k_cc_union(const uint8_t* __restrict__ raw, KParams p, int* lab) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N || raw[c] != T_GAS) return;
+  int x, y, z;
+  decode(p, c, x, y, z);
+  for (int i = 1; i < Q; ++i) {
+    const int n = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+    if (n < 0 || n >= c || raw[n] != T_GAS) continue;  // each pair once
+    int a = cc_find(lab, c), b = cc_find(lab, n);
+    while (a != b) {
+      if (a > b) {
+        const int t = a;
+        a = b;
+        b = t;
+      }
+      const int old = atomicCAS(&lab[b], b, a);  // hook root b under a
+      if (old == b) break;
+      b = cc_find(lab, old);
+      a = cc_find(lab, a);
+    }
+  }
+}
+
+static __global__ void k_cc_compress(int N, int* lab) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N && lab[c] >= 0) lab[c] = cc_find(lab, c);
+}
+
+// Roots per block of kCcChunk cells (pass 1 of the numbering).
+constexpr int kCcChunk = 1024;
+static __global__ void k_cc_count(int N, const int* __restrict__ lab, int* block_roots) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int k = threadIdx.x; k < kCcChunk; k += blockDim.x) {
+    const long long c = (long long)blockIdx.x * kCcChunk + k;
+    if (c < N && lab[c] == (int)c) ++mine;
+  }
+  atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) block_roots[blockIdx.x] = cnt;
+}
+
+// Exclusive scan of the per-block root counts (one block); total in off[n].
+static __global__ void k_cc_scan(int nblocks, const int* __restrict__ block_roots, int* off) {
+  block_prefix(nblocks, off, [&](int k) { return block_roots[k]; });
+}
+
+// Bubble id of every root in index order (pass 2): warps walk their block's
+// chunk in order, so ranks within the chunk follow the cell index.
+static __global__ void k_cc_number(int N, const int* __restrict__ lab, const int* __restrict__ off,
+                                   int* root_id) {
+  __shared__ int base;
+  if (threadIdx.x == 0) base = off[blockIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  // one warp numbers the chunk sequentially in 32-cell steps
+  if (threadIdx.x < 32) {
+    int b = base;
+    for (int k = 0; k < kCcChunk; k += 32) {
+      const long long c = (long long)blockIdx.x * kCcChunk + k + lane;
+      const bool root = c < N && lab[c] == (int)c;
+      const unsigned m = __ballot_sync(0xffffffffu, root);
+      if (root) root_id[c] = b + __popc(m & ((1u << lane) - 1u));
+      b += __popc(m);
+    }
+  }
+}
+
+// Bubble id of gas cells (their root's number) and of interface cells (the
+// lowest id among their gas neighbours); -1 elsewhere.
+template <int Q>
+__global__ void k_cc_assign(const uint8_t* __restrict__ raw, KParams p, const int* __restrict__ lab,
+                            const int* __restrict__ root_id, int* bid) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const uint8_t t = raw[c];
+  if (t == T_GAS) {
+    bid[c] = root_id[lab[c]];
+    return;
+  }
+  int best = -1;
+  if (t == T_IFACE) {
+    int x, y, z;
+    decode(p, c, x, y, z);
+    for (int i = 1; i < Q; ++i) {
+      const int n = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+      if (n < 0 || raw[n] != T_GAS) continue;
+      const int b = root_id[lab[n]];
+      if (best < 0 || b < best) best = b;
+    }
+  }
+  bid[c] = best;
+}
+
+// Initial bubble volumes in 2^-32 fixed point: gas cells count 1, interface
+// cells 1 - phi (the same terms as the step's volume sums).
+static __global__ void k_cc_volumes(const uint8_t* __restrict__ raw, const double* __restrict__ fill,
+                                    int N, const int* __restrict__ bid, long long* gas_cnt,
+                                    long long* iface_fix) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int b = -1;
+  long long g = 0, v = 0;
+  if (c < N) {
+    b = bid[c];
+    if (b >= 0 && raw[c] == T_GAS) g = 1;
+    if (b >= 0 && raw[c] == T_IFACE) v = __double2ll_rn((1.0 - fill[c]) * 4294967296.0);
+  }
+  unsigned remaining = __ballot_sync(0xffffffffu, b >= 0);
+  while (remaining) {
+    const int leader = __ffs(remaining) - 1;
+    const int bb = __shfl_sync(0xffffffffu, b, leader);
+    const bool mine = b == bb;
+    long long sg = mine ? g : 0, sv = mine ? v : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if (lane == leader) {
+      if (sg) atomicAdd((unsigned long long*)&gas_cnt[bb], (unsigned long long)sg);
+      if (sv) atomicAdd((unsigned long long*)&iface_fix[bb], (unsigned long long)sv);
+    }
+    remaining &= ~__ballot_sync(0xffffffffu, mine);
+  }
+}
+
+static __global__ void k_cc_v0(int nb, const long long* gas_cnt, long long* iface_fix, double* V0,
+                               double* Vcur, double* pV, double pv0) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const long long acc = gas_cnt[b] * 4294967296LL + iface_fix[b];
+  const double V = __ll2double_rn(acc) / 4294967296.0;
+  V0[b] = V;
+  Vcur[b] = V;
+  pV[b] = pv0;
+  iface_fix[b] = 0;
 }
 
 // ------------------------------------------------------------- geometry
@@ -387,6 +632,12 @@ constexpr int GB = GE * GE * GE;         // 2744 box positions
 constexpr int GS = GT + 4;               // phi~ sub-box edge (12)
 constexpr int GN = GT + 2;               // n^ sub-box edge (10)
 constexpr int kGeoBlock = 256;
+// geometry blocks per interface-band block: each tile's block runs four
+// dependent shared-memory phases, so many resident tiles hide the latency
+#ifndef FSLBM_GEO_MULT
+#define FSLBM_GEO_MULT 3
+#endif
+constexpr int kGeoGridMult = FSLBM_GEO_MULT;
 
 template <class R>
 constexpr size_t geometry_smem() {
@@ -550,71 +801,23 @@ __global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int 
 // ------------------------------------------------------------ bulk sweep
 // Pull stream-collide of liquid cells (Eqs. nm-lbm-streaming, -collision)
 // with bounce-back at obstacles.  Interface and gas cells are skipped.
-// One thread per cell over the whole grid, 256 consecutive cells per block
-// (coalesced rows of the SoA slices).  Interior cells pull from constant
-// index offsets; cells next to a wall or across a periodic face take the
-// general neighbour path.
+//
+// Bounce-back through the obstacle's slot: a fluid cell x whose pull source
+// x - c_i is an obstacle cell writes, besides its own PDFs, f*_ibar(x) into
+// slot i of that obstacle cell.  That slot is pulled by x alone, so the write
+// is race-free, and next step x pulls its bounced-back PDF from the constant
+// offset like any interior cell: the bulk sweep reads at constant offsets
+// except next to a non-periodic domain face (own-slot bounce-back) or across
+// a periodic face (wrapped index), which take the general path.  Every
+// kernel that produces post-collision PDFs of a fluid cell (bulk, interface,
+// new interface cells, init) writes these reflected copies.
 constexpr int kBulkBlock = 256;
 
+// One liquid cell, loads straight from global memory (storage formats of
+// 2 bytes, and batches).
 template <int Q, class S, int COLL>
 __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
-                                          uint8_t fl, bool general, bool wrap);
-
-// Persistent sweep: each warp takes 32 / kSegCells groups of the liquid
-// group list (runs of consecutive cells of the SoA slices, so loads and
-// stores coalesce per group).  Gas and obstacle lanes that share a 32-byte
-// sector of a PDF slice with a liquid lane store zero PDFs (their values are
-// never read): the sector is then written whole, which spares HBM a
-// read-modify-write of it.  Interface lanes store nothing (the interface
-// kernel writes them concurrently).
-#ifndef FSLBM_BULK_FILL
-#define FSLBM_BULK_FILL 1
-#endif
-// One warp's share of the bulk sweep: groups [w G, w G + G) of the liquid
-// group list, G = 32 / kSegCells (every lane of the warp calls it).
-template <int Q, class S, int COLL>
-__device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int parity, int w,
-                                          int nseg) {
-  using T = typename S::T;
-  using R = typename S::Real;
-  constexpr int kGroups = 32 / kSegCells;
-  constexpr int kFill = (32 / (int)sizeof(T)) < kSegCells ? (32 / (int)sizeof(T)) : kSegCells;
-  const int lane = threadIdx.x & 31;
-
-    const int e = w * kGroups + lane / kSegCells;
-    const int c = e < nseg ? d.segs[e] * kSegCells + (lane % kSegCells) : p.N;
-    const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_IFACE;
-    const int t = fl & F_TYPE;
-    const bool liq = t == T_LIQ;
-    // the whole warp takes the general path when one of its cells needs it
-    const bool general = __any_sync(0xffffffffu, liq && (fl & (F_NEAR_WALL | F_WRAP)));
-    const bool wrap = __any_sync(0xffffffffu, liq && (fl & F_WRAP));
-    const unsigned lm = __ballot_sync(0xffffffffu, liq);
-    if (liq) {
-      bulk_cell<Q, S, COLL>(d, p, parity, c, fl, general, wrap);
-    } else if (FSLBM_BULK_FILL) {
-      const unsigned grp = (lm >> (lane & ~(kFill - 1))) & ((1u << kFill) - 1u);
-      if (grp && t != T_IFACE) {
-        T* __restrict__ B = (T*)d.pdf[parity ^ 1];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
-      }
-    }
-  }
-
-template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
-    k_bulk(DPtrs d, KParams p, int parity) {
-  constexpr int kGroups = 32 / kSegCells;
-  const int nseg = d.counts[5];
-  const int warps = (gridDim.x * kBulkBlock) >> 5;
-  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
-    bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
-}
-
-template <int Q, class S, int COLL>
-__device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
-                                          uint8_t fl, bool general, bool wrap) {
+                                          uint8_t fl, bool general) {
   using R = typename S::Real;
   using T = typename S::T;
   const T* __restrict__ A = (const T*)d.pdf[parity];
@@ -625,41 +828,67 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
     const T* Ac = A + c;
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(Ac[p.dofs[i]], i);
-  } else if (!wrap) {
-    // bounce-back directions from the static wall mask
-    const uint32_t wm = (fl & F_NEAR_WALL) ? d.wallmask[c] : 0u;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const bool bb = (wm >> i) & 1u;
-      const long long idx = bb ? (long long)OPP(i) * Np + c : p.dofs[i] + c;
-      f[i] = load_w<S, Q>(A[idx], i);
-    }
   } else {
-    // bounce-back directions from the static wall mask; pull sources across
-    // periodic faces by branch-free index corrections
     int x, y, z;
     decode(p, c, x, y, z);
-    const uint32_t wm = (fl & F_NEAR_WALL) ? d.wallmask[c] : 0u;
-    const int nxy = p.nx * p.ny;
-    const int cxp = (x == 0) ? p.nx : 0, cxm = (x == p.nx - 1) ? -p.nx : 0;
-    const int cyp = (y == 0) ? nxy : 0, cym = (y == p.ny - 1) ? -nxy : 0;
-    const int czp = (z == 0) ? p.N : 0, czm = (z == p.nz - 1) ? -p.N : 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int corr = (CX(i) == 1 ? cxp : CX(i) == -1 ? cxm : 0) +
-                       (CY(i) == 1 ? cyp : CY(i) == -1 ? cym : 0) +
-                       (CZ(i) == 1 ? czp : CZ(i) == -1 ? czm : 0);
-      const long long idx = ((wm >> i) & 1u) ? (long long)OPP(i) * Np + c
-                                              : (long long)i * Np + (c - p.off[i] + corr);
-      f[i] = load_w<S, Q>(A[idx], i);
-    }
+    for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(A[pull_index_general<Q>(p, c, x, y, z, i)], i);
   }
   bool bad = false;
   collide_any<Q, S, COLL>(f, p, bad);
   T* Bc = B + c;
 #pragma unroll
   for (int i = 0; i < Q; ++i) Bc[(long long)i * Np] = store_w<S, Q>(f[i], i);
+  if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], general, f);
   if (bad) d.err[0] = 1;
+}
+
+// One warp's share of the direct bulk sweep: groups [w G, w G + G) of the
+// liquid group list, G = 32 / kSegCells (every lane of the warp calls it).
+// Gas lanes that share a 32-byte sector of a PDF slice with a liquid lane
+// store zero PDFs (gas values are never read): the sector is then written
+// whole, which spares HBM a read-modify-write of it.  Interface lanes (the
+// interface kernel writes them concurrently) and obstacle lanes (reflected
+// copies) store nothing.
+#ifndef FSLBM_BULK_FILL
+#define FSLBM_BULK_FILL 1
+#endif
+template <int Q, class S, int COLL>
+__device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int parity, int w,
+                                          int nseg) {
+  using T = typename S::T;
+  using R = typename S::Real;
+  constexpr int kGroups = 32 / kSegCells;
+  constexpr int kFill = (32 / (int)sizeof(T)) < kSegCells ? (32 / (int)sizeof(T)) : kSegCells;
+  const int lane = threadIdx.x & 31;
+  const int e = w * kGroups + lane / kSegCells;
+  const int c = e < nseg ? d.segs[e] * kSegCells + (lane % kSegCells) : p.N;
+  const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_IFACE;
+  const int t = fl & F_TYPE;
+  const bool liq = t == T_LIQ;
+  // the whole warp takes the general path when one of its cells needs it
+  const bool general = __any_sync(0xffffffffu, liq && (fl & (F_FACE | F_WRAP)));
+  const unsigned lm = __ballot_sync(0xffffffffu, liq);
+  if (liq) {
+    bulk_cell<Q, S, COLL>(d, p, parity, c, fl, general);
+  } else if (FSLBM_BULK_FILL) {
+    const unsigned grp = (lm >> (lane & ~(kFill - 1))) & ((1u << kFill) - 1u);
+    if (grp && t == T_GAS) {
+      T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
+    }
+  }
+}
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
+    k_bulk(DPtrs d, KParams p, int parity) {
+  constexpr int kGroups = 32 / kSegCells;
+  const int nseg = d.counts[5];
+  const int warps = (gridDim.x * kBulkBlock) >> 5;
+  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
+    bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
 }
 
 // ------------------------------------------------------- interface update
@@ -790,6 +1019,10 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
+    }
+    {
+      const uint8_t fl = flags[c];
+      if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], (fl & F_WRAP) != 0, f);
     }
     const double phin = mn / rho;
     d.m_next[k] = mn;
@@ -968,16 +1201,17 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
         ub1 = sy / (double)cnt;
         ub2 = sz / (double)cnt;
       }
-      if constexpr (S::kDev) {
+      R fn[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-          B[(long long)i * Np + c] =
-              S::stored(feq_dev<Q, R>(i, R(rb - 1.0), R(rb), R(ub0), R(ub1), R(ub2)));
-      } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          B[(long long)i * Np + c] = S::store(feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2)), W<Q, R>(i));
+      for (int i = 0; i < Q; ++i) {
+        if constexpr (S::kDev)
+          fn[i] = feq_dev<Q, R>(i, R(rb - 1.0), R(rb), R(ub0), R(ub1), R(ub2));
+        else
+          fn[i] = feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2));
+        B[(long long)i * Np + c] = store_w<S, Q>(fn[i], i);
       }
+      const uint8_t fl = d.flags[c];
+      if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], (fl & F_WRAP) != 0, fn);
       const double m = 0.0 + s;
       d.mass[c] = m;
       d.phi[c] = m / rb;
@@ -1252,43 +1486,6 @@ __device__ __forceinline__ int find_domain(const int* __restrict__ off, int n, i
     else hi = mid;
   }
   return lo;
-}
-
-// Block-wide exclusive prefix sum of per-domain values (one block; values
-// produced by f(k) for k < n) into off[0..n].
-template <class F>
-__device__ __forceinline__ void block_prefix(int n, int* off, F f) {
-  __shared__ int carry;
-  __shared__ int wsum[32];
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int k = base + threadIdx.x;
-    const int v = k < n ? f(k) : 0;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      int t = lane < nw ? wsum[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      wsum[lane] = t;
-    }
-    __syncthreads();
-    const int incl = x + (wid > 0 ? wsum[wid - 1] : 0) + carry;
-    if (k < n) off[k + 1] = incl;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = incl;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) off[0] = 0;
 }
 
 __device__ __forceinline__ int round32(int v) { return (v + 31) & ~31; }

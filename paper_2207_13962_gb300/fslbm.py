@@ -49,6 +49,30 @@ class fslbm_obs(C.Structure):
                 ("liquid_volume", C.c_double)]
 
 
+class fslbm_server_config(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("collision", C.c_int), ("precision", C.c_int),
+                ("max_active", C.c_int), ("chunk_steps", C.c_int), ("memory_budget", C.c_int64),
+                ("stream", C.c_void_p)]
+
+
+class fslbm_request(C.Structure):
+    _fields_ = [("domain", fslbm_domain), ("bc_variant", C.c_int), ("params", fslbm_params),
+                ("fill", C.c_void_p), ("flags", C.c_void_p), ("velocity", C.c_void_p),
+                ("density", C.c_void_p), ("steps", C.c_int)]
+
+
+class fslbm_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("steps", C.c_int64), ("cells", C.c_int64),
+                ("obs", fslbm_obs), ("t_queue", C.c_double), ("t_result", C.c_double)]
+
+
+class fslbm_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("queued", C.c_int), ("active", C.c_int), ("max_active_seen", C.c_int),
+                ("batch_rebuilds", C.c_int64), ("batch_steps", C.c_int64), ("cell_updates", C.c_double),
+                ("memory_used", C.c_int64), ("memory_budget", C.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -59,7 +83,9 @@ SYMBOLS = ["fslbm_params_default", "fslbm_create", "fslbm_init", "fslbm_step", "
            "fslbm_observables_noalloc", "fslbm_destroy", "fslbm_last_error", "fslbm_version",
            "fslbm_batch_create", "fslbm_batch_step", "fslbm_batch_sync", "fslbm_batch_autotune",
            "fslbm_batch_set_tuning", "fslbm_batch_get_tuning", "fslbm_batch_launches",
-           "fslbm_batch_destroy", "fslbm_batch_last_error"]
+           "fslbm_batch_destroy", "fslbm_batch_last_error", "fslbm_memory_estimate",
+           "fslbm_server_create", "fslbm_server_submit", "fslbm_server_poll", "fslbm_server_result",
+           "fslbm_server_stats_get", "fslbm_server_destroy", "fslbm_server_last_error"]
 
 
 def load(build_if_missing: bool = True):
@@ -131,6 +157,22 @@ def load(build_if_missing: bool = True):
         lib.fslbm_batch_destroy.restype = None
         lib.fslbm_batch_last_error.argtypes = [p]
         lib.fslbm_batch_last_error.restype = C.c_char_p
+        lib.fslbm_memory_estimate.argtypes = [C.POINTER(fslbm_domain), i, i, i, C.POINTER(C.c_size_t)]
+        lib.fslbm_memory_estimate.restype = i
+        lib.fslbm_server_create.argtypes = [C.POINTER(fslbm_server_config), C.POINTER(p)]
+        lib.fslbm_server_create.restype = i
+        lib.fslbm_server_submit.argtypes = [p, C.POINTER(fslbm_request), C.POINTER(C.c_int64)]
+        lib.fslbm_server_submit.restype = i
+        lib.fslbm_server_poll.argtypes = [p, C.POINTER(i)]
+        lib.fslbm_server_poll.restype = i
+        lib.fslbm_server_result.argtypes = [p, C.c_int64, C.POINTER(fslbm_result), p, p]
+        lib.fslbm_server_result.restype = i
+        lib.fslbm_server_stats_get.argtypes = [p, C.POINTER(fslbm_server_stats)]
+        lib.fslbm_server_stats_get.restype = i
+        lib.fslbm_server_destroy.argtypes = [p]
+        lib.fslbm_server_destroy.restype = None
+        lib.fslbm_server_last_error.argtypes = [p]
+        lib.fslbm_server_last_error.restype = C.c_char_p
         _lib = lib
         return lib
 
@@ -336,6 +378,114 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _params_for(sc, precision, **over):
+    """fslbm_params of a scenario (keywords as for Context)."""
+    lib = load()
+    kw = dict(omega=sc.omega, g=sc.g, sigma=sc.sigma, bubble_model=sc.bubble_model)
+    kw.update({k: v for k, v in over.items() if k in ("omega", "g", "sigma", "bubble_model", "trt_magic",
+                                                      "eps_phi", "p_v0", "om3_fallback")})
+    prm = fslbm_params()
+    lib.fslbm_params_default(C.byref(prm))
+    prm.omega = float(kw["omega"])
+    prm.g = (C.c_double * 3)(*[float(x) for x in kw["g"]])
+    prm.sigma = float(kw["sigma"])
+    prm.bubble_model = int(bool(kw["bubble_model"]))
+    for k in ("trt_magic", "eps_phi", "p_v0"):
+        if k in kw:
+            setattr(prm, k, float(kw[k]))
+    if "om3_fallback" in kw:
+        prm.om3_fallback = VARIANT[kw["om3_fallback"]]
+    prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    return prm
+
+
+class Server:
+    """Continuous-batching request loop (wraps ``fslbm_server``)."""
+
+    def __init__(self, q=19, collision="TRT", precision="FP32", max_active=16, chunk_steps=100,
+                 memory_budget=0, stream=None):
+        self.lib = load()
+        cfg = fslbm_server_config(LATTICE[q], COLLISION[collision], PRECISION[precision], int(max_active),
+                                  int(chunk_steps), int(memory_budget), C.c_void_p(int(stream)) if stream else None)
+        self.precision = precision
+        h = C.c_void_p()
+        st = self.lib.fslbm_server_create(C.byref(cfg), C.byref(h))
+        if st != OK:
+            raise FslbmError(st, "fslbm_server_create failed")
+        self.h = h
+        self.shapes = {}
+
+    def _check(self, st):
+        if st != OK:
+            raise FslbmError(st, self.lib.fslbm_server_last_error(self.h).decode())
+        return st
+
+    def submit(self, sc, steps, **over):
+        """Queue scenario ``sc`` for ``steps`` steps; returns the request id."""
+        fill = np.ascontiguousarray(sc.fill, np.float64)
+        flags = np.ascontiguousarray(sc.flags, np.uint8)
+        vel = None if sc.velocity is None else np.ascontiguousarray(sc.velocity, np.float64)
+        den = None if sc.density is None else np.ascontiguousarray(sc.density, np.float64)
+        rq = fslbm_request()
+        rq.domain = fslbm_domain(*sc.shape, (C.c_int * 3)(*[int(bool(x)) for x in sc.periodic]))
+        rq.bc_variant = VARIANT[over.get("variant", sc.variant)]
+        rq.params = _params_for(sc, self.precision, **over)
+        rq.fill, rq.flags = fill.ctypes.data, flags.ctypes.data
+        rq.velocity = None if vel is None else vel.ctypes.data
+        rq.density = None if den is None else den.ctypes.data
+        rq.steps = int(steps)
+        rid = C.c_int64(0)
+        self._check(self.lib.fslbm_server_submit(self.h, C.byref(rq), C.byref(rid)))
+        self.shapes[rid.value] = sc.N
+        return rid.value
+
+    def poll(self):
+        n = C.c_int(0)
+        self._check(self.lib.fslbm_server_poll(self.h, C.byref(n)))
+        return n.value
+
+    def result(self, rid):
+        """Final fields and timing of a finished run, or None while it runs."""
+        N = self.shapes[rid]
+        res = fslbm_result()
+        fill = np.zeros(N, np.float64)
+        flags = np.zeros(N, np.uint8)
+        st = self.lib.fslbm_server_result(self.h, rid, C.byref(res), fill.ctypes.data, flags.ctypes.data)
+        if st == ESTATE:
+            return None
+        self._check(st)
+        obs = {k: getattr(res.obs, k) for k, _ in fslbm_obs._fields_}
+        return {"id": res.id, "status": res.status, "steps": res.steps, "cells": res.cells, "obs": obs,
+                "t_queue": res.t_queue, "t_result": res.t_result, "fill": fill, "flags": flags}
+
+    def stats(self):
+        st = fslbm_server_stats()
+        self._check(self.lib.fslbm_server_stats_get(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in fslbm_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fslbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def memory_estimate(shape, q=19, precision="FP32", with_velocity=False):
+    lib = load()
+    b = C.c_size_t(0)
+    dom = fslbm_domain(*shape, (C.c_int * 3)(0, 0, 0))
+    st = lib.fslbm_memory_estimate(C.byref(dom), LATTICE[q], PRECISION[precision], int(bool(with_velocity)),
+                                   C.byref(b))
+    if st != OK:
+        raise FslbmError(st, "fslbm_memory_estimate failed")
+    return b.value
 
 
 def context_for(sc, precision="FP64", stream=None, **over):

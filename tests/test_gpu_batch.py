@@ -1,8 +1,11 @@
 """Batches: uneven domains advanced by one launch per phase over a block table
 (``fslbm_batch_*``).  The batched kernels run the same per-cell bodies as
-the single-domain ones, so every member must match a copy of it stepped
-alone bit for bit, whatever the mix of sizes, variants, parities and
-interleaved single-context calls.  The single-domain path itself is pinned
+the single-domain ones, so in FP64 (compiled without multiply-add
+contraction) every member must match a copy of it stepped alone bit for bit,
+whatever the mix of sizes, variants, parities and interleaved
+single-context calls.  In FP32 the compiler may contract multiply-adds
+differently in the two kernels, so FP32 members agree to FP32 rounding
+(flags identical, PDFs within 1e-6).  The single-domain path itself is pinned
 to the oracle by test_gpu_parity.py; one member here is also compared with
 the oracle directly."""
 import numpy as np
@@ -98,7 +101,10 @@ def test_batch_fp32_d3q27_cylinders(gpu_lib):
     for a in alone:
         a.step(60)
     for k, (a, m) in enumerate(zip(alone, members)):
-        _assert_same(a, m, f"cylinder {k}")
+        ra, rm = a.read(), m.read()
+        np.testing.assert_array_equal(ra["flags"], rm["flags"], err_msg=f"cylinder {k}")
+        assert np.abs(ra["pdf"] - rm["pdf"]).max() <= 1e-6, f"cylinder {k}"
+        assert np.abs(ra["fill"] - rm["fill"]).max() <= 1e-6, f"cylinder {k}"
     batch.close()
 
 
