@@ -129,6 +129,33 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
+KERNEL_SOURCES = ("paper_2207_13962_gb300/csrc/fslbm_kernels.cuh", "paper_2207_13962_gb300/csrc/fslbm_common.cuh")
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 of the kernel sources (the ncu traffic applies only to them)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def bulk_traffic(n_liquid: float, precision: str):
+    """DRAM bytes per bulk launch from the committed ncu capture
+    (profiles/k_bulk_traffic.json), scaled by liquid cells; None when the
+    kernel sources changed since the capture or the precision differs."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_bulk_traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("kernel_source_sha256") != kernel_source_hash() or t.get("precision") != precision:
+        return None
+    return t["dram_bytes_per_launch"] * n_liquid / t["liquid_cells"]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -248,10 +275,9 @@ def bench_ours(args, ws, rank, local):
     obs2 = ctx.observables()
     bulk_ms = times["bulk"] / args.steps
     n_liq = 0.5 * (obs1["n_liquid"] + obs2["n_liquid"])
-    nseg = ctx.work_counts()["liquid_segments"]
-    # algorithmic bytes of one bulk launch: read + write q PDFs per liquid
-    # cell, one flag byte per cell of the swept 32-cell groups
-    alg_bytes = n_liq * 2 * Q * S_BYTES[prec] + nseg * 32
+    # algorithmic bytes of one bulk launch: read + write q PDFs and read one
+    # flag byte per liquid cell (the sweep visits liquid cells only)
+    alg_bytes = n_liq * (2 * Q * S_BYTES[prec] + 1)
     achieved = alg_bytes / (bulk_ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -335,7 +361,9 @@ def bench_ours(args, ws, rank, local):
                 "bound": "hbm", "kernel": "k_bulk (pull stream-collide of liquid cells)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
-                "traffic": None,
+                "traffic": (round(bulk_traffic(n_liq, prec)) if bulk_traffic(n_liq, prec) else None),
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
+                                "160x160x256 profiling case, scaled by liquid cells (profiles/k_bulk_traffic.json)",
                 "alg_bytes_per_launch": int(alg_bytes), "launch_ms": round(bulk_ms, 6),
                 "stage_share": share,
             },

@@ -213,7 +213,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   c->band_grid = sms * 2;
   // the persistent bulk sweep leaves FSLBM_BULK_RESERVE block slots per SM to
   // the interface-band kernels that run beside it
-  c->bulk_grid = sms * (c->ops.bulk_blocks_per_sm - FSLBM_BULK_RESERVE) * FSLBM_BULK_WAVES;
+  c->bulk_grid = sms * (c->ops.bulk_blocks_per_sm - FSLBM_BULK_RESERVE);
 
   DPtrs& d = c->d;
   std::memset(&d, 0, sizeof(d));

@@ -19,12 +19,6 @@
 #ifndef FSLBM_BULK_RESERVE
 #define FSLBM_BULK_RESERVE 0
 #endif
-// The bulk sweep's grid holds this many waves of resident blocks; with more
-// than one, blocks retire during the sweep and the higher-priority band
-// kernels take their slots.
-#ifndef FSLBM_BULK_WAVES
-#define FSLBM_BULK_WAVES 1
-#endif
 
 struct fslbm_ctx {
   fslbm_domain dom;
