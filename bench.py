@@ -179,6 +179,9 @@ def make_workload(name: str, variant: str):
     elif name == "dam_break":
         sc = S.dam_break(variant=variant)
         desc = "rectangular dam break 256x128x64, column 64^3, D3Q19 TRT, g=1e-5, nu=1e-3, no-slip"
+    elif name == "box256":
+        sc = S.flat_interface(nx=256, ny=256, nz=256, depth=249.5, g=1e-5, variant=variant)
+        desc = "256^3 liquid box with a flat surface (bulk ceiling, profiling case), D3Q19 TRT"
     elif name == "box512":
         sc = S.flat_interface(nx=512, ny=512, nz=512, depth=505.5, g=1e-5, variant=variant)
         desc = "512^3 liquid box with a flat surface (bulk ceiling), D3Q19 TRT"
@@ -201,8 +204,8 @@ def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50):
         smp = oracle_sample(sc, name, 352, 416)
     elif name == "taylor_bubble_256":
         smp = oracle_sample(sc, name, 128, 160)
-    elif name == "box512":
-        smp = oracle_sample(sc, name, 448, 512)
+    elif name in ("box256", "box512"):
+        smp = oracle_sample(sc, name, sc.shape[2] - 64, sc.shape[2])
     else:
         smp = sc
     o = Oracle(*smp.shape, **S.make_oracle_kwargs(smp))
@@ -582,7 +585,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "taylor_bubble_256", "dam_break", "box512",
+    ap.add_argument("--workload", default="taylor_bubble", choices=["taylor_bubble", "taylor_bubble_256", "dam_break", "box256", "box512",
                                                        "batch_cylinders", "serve_drops"])
     ap.add_argument("--precision", default="FP32", choices=list(S_BYTES))
     ap.add_argument("--variant", default="OM", choices=["NBRC", "NBKC", "OM", "OM3"])

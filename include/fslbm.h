@@ -162,8 +162,9 @@ fslbm_status fslbm_bubbles(fslbm_ctx* ctx, double* volume, double* pressure,
 /* Opt-in per-stage CUDA-event timing of the next steps (0 disables).  While
  * enabled, fslbm_step launches kernels one by one (no CUDA graph). */
 fslbm_status fslbm_set_timing(fslbm_ctx* ctx, int enable);
-/* Accumulated milliseconds per stage since timing was enabled, in the order
- * geometry, bulk, interface, convert, bubbles; writes min(cap, 5) values. */
+/* Accumulated milliseconds per stage since timing was enabled, one stage per
+ * kernel of the step in the order geometry, bulk, interface, resolve, count,
+ * apply, finalize, bubbles; writes min(cap, 8) values. */
 fslbm_status fslbm_stage_times(fslbm_ctx* ctx, double* ms, int cap, int* n_launches);
 
 /* Checkpoint of the full state (PDFs, flags, fill, mass, bubbles, step) into

@@ -235,6 +235,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   ALLOC(d.conv, n4);
   ALLOC(d.cfin, n4);
   ALLOC(d.claim, n4);
+  ALLOC(d.rcv, n4);
   ALLOC(d.share, N * sizeof(double));
   ALLOC(d.band[0], N * sizeof(int));
   ALLOC(d.band[1], N * sizeof(int));
@@ -249,6 +250,8 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   ALLOC(d.newlist, N * sizeof(int));
   ALLOC(d.nhat, 3 * N * rs);
   ALLOC(d.rhog, N * rs);
+  ALLOC(d.mom_rho, N * sizeof(double));
+  ALLOC(d.mom_u, 3 * N * rs);
   ALLOC(d.m_next, N * sizeof(double));
   ALLOC(d.phi_next, N * sizeof(double));
   ALLOC(d.rho_band, N * sizeof(double));
@@ -262,6 +265,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.claim, 0, n4, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.rcv, 0, n4, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.tile_mark, 0, ntiles * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4 * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -291,9 +295,9 @@ fslbm_status fslbm_memory_estimate(const fslbm_domain* domain, fslbm_lattice lat
       (size_t)((domain->nx + 7) / 8) * ((domain->ny + 7) / 8) * ((domain->nz + 7) / 8);
   const size_t nseg = (N + kSegCells - 1) / kSegCells;
   size_t b = 2 * (size_t)lattice * Np * elem;            // PDFs, two buffers
-  b += 6 * n4;                                           // flags, cls, mark, conv, cfin, claim
+  b += 7 * n4;                                           // flags, cls, mark, conv, cfin, claim, rcv
   b += N * (4 + 8 + 8 + 4 + 8 + 4 + 4 + 4);              // wallmask phi mass bid share band[2] newlist
-  b += N * (4 * rs + 3 * 8);                             // nhat rhog m_next phi_next rho_band
+  b += N * (7 * rs + 4 * 8);                             // nhat rhog mom m_next phi_next rho_band
   b += 3 * ntiles * 4 + 2 * nseg * 4 + 4096;             // tiles, segments, counters, partials
   b += N * (1 + 8 + 8) + (with_velocity ? 24 * N : 0);   // fslbm_init staging (peak)
   *bytes = b;
@@ -425,6 +429,11 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(d.counts, 0, 8 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4 * sizeof(int), st);
+  // a context initialised again still holds the tile marks of its last step
+  if (e == cudaSuccess) {
+    const size_t nt = (size_t)((c->dom.nx + 7) / 8) * ((c->dom.ny + 7) / 8) * ((c->dom.nz + 7) / 8);
+    e = cudaMemsetAsync(d.tile_mark, 0, nt * sizeof(int), st);
+  }
   if (e == cudaSuccess) {
     k_compact_full<<<(c->kp.N + kBlock - 1) / kBlock, kBlock, 0, st>>>(d.flags, c->kp.N, d.band[0],
                                                                       &d.counts[0]);
@@ -461,10 +470,9 @@ fslbm_status fslbm_step(fslbm_ctx* c, int n) {
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaEventSynchronize(c->ev.ev[StageEvents::kMarks - 1]);
       if (e == cudaSuccess) {
-        const int map[5][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < StageEvents::kStages; ++k) {
           float ms = 0.f;
-          cudaEventElapsedTime(&ms, c->ev.ev[map[k][0]], c->ev.ev[map[k][1]]);
+          cudaEventElapsedTime(&ms, c->ev.ev[k], c->ev.ev[k + 1]);
           c->stage_ms[k] += ms;
         }
       }
@@ -574,14 +582,14 @@ fslbm_status fslbm_set_timing(fslbm_ctx* c, int enable) {
     c->ev_made = true;
   }
   c->timing = enable != 0;
-  for (int k = 0; k < 5; ++k) c->stage_ms[k] = 0.0;
+  for (int k = 0; k < StageEvents::kStages; ++k) c->stage_ms[k] = 0.0;
   c->launches = 0;
   return FSLBM_OK;
 }
 
 fslbm_status fslbm_stage_times(fslbm_ctx* c, double* ms, int cap, int* n_launches) {
   if (!c) return FSLBM_EINVAL;
-  for (int k = 0; k < 5 && k < cap; ++k) ms[k] = c->stage_ms[k];
+  for (int k = 0; k < StageEvents::kStages && k < cap; ++k) ms[k] = c->stage_ms[k];
   if (n_launches) *n_launches = (int)c->launches;
   return FSLBM_OK;
 }

@@ -196,6 +196,8 @@ struct DPtrs {
   uint8_t* conv;
   uint8_t* cfin;
   uint8_t* claim;
+  uint8_t* rcv;    // 1: an interface cell next to a cell that converts this
+                   // step (set by the count kernel, cleared by apply)
   double* share;
   int* band[2];
   int* counts;   // [0],[1]: band list counts; [2]: new-cell list count;
@@ -207,6 +209,9 @@ struct DPtrs {
   int* newlist;
   void* nhat;    // Real[3 * cap]
   void* rhog;    // Real[cap]
+  double* mom_rho;  // rho and u of the interface cells' post-collision PDFs,
+  void* mom_u;      // (Real[3 * N]) written by the interface kernel in the
+                    // same arithmetic as post_moments, read for new cells
   double* m_next;
   double* phi_next;
   double* rho_band;

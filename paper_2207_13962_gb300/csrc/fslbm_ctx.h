@@ -39,7 +39,7 @@ struct fslbm_ctx {
   bool timing = false;
   fslbm::StageEvents ev;
   bool ev_made = false;
-  double stage_ms[5] = {0, 0, 0, 0, 0};
+  double stage_ms[fslbm::StageEvents::kStages] = {};
   long long launches = 0;
   double* d_obs = nullptr;
   std::vector<void*> allocs;

@@ -62,13 +62,16 @@ struct Engine {
       k_interface<Q, S, 1><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
     if (ev) ev->mark(3, st);
     k_resolve<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+    if (ev) ev->mark(4, st);
     k_count<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+    if (ev) ev->mark(5, st);
     if (forked) cudaStreamWaitEvent(st, fk->join, 0);
     k_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+    if (ev) ev->mark(6, st);
     k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
-    if (ev) ev->mark(4, st);
+    if (ev) ev->mark(7, st);
     if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
-    if (ev) ev->mark(5, st);
+    if (ev) ev->mark(8, st);
   }
 
   // One step of all domains of a block table.  Same stages and stream fork

@@ -9,10 +9,11 @@
 
 namespace fslbm {
 
-// CUDA events between the stages of a step (geometry, bulk, interface,
-// conversion, bubbles) for opt-in per-stage timing.
+// CUDA events between the kernels of a step (geometry, bulk, interface,
+// resolve, count, apply, finalize, bubbles) for opt-in per-stage timing.
 struct StageEvents {
-  static constexpr int kMarks = 6;
+  static constexpr int kMarks = 9;
+  static constexpr int kStages = kMarks - 1;
   cudaEvent_t ev[kMarks];
   void mark(int i, cudaStream_t st) { cudaEventRecord(ev[i], st); }
 };

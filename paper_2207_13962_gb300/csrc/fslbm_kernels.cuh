@@ -416,12 +416,13 @@ __global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __re
                        // slots receive their neighbours' reflected copies)
   R fe[Q];
   if constexpr (S::kDev) {
-    // deviation f^eq - w formed in FP64, rounded once to the stored format
-    const double ux = vel ? vel[c] : 0.0;
-    const double uy = vel ? vel[(long long)p.N + c] : 0.0;
-    const double uz = vel ? vel[2LL * p.N + c] : 0.0;
+    // deviation f^eq - w in FP32 from drho = rho - 1 taken in FP64 (every
+    // term is then of the size of a deviation)
+    const R ux = vel ? R(vel[c]) : R(0.0);
+    const R uy = vel ? R(vel[(long long)p.N + c]) : R(0.0);
+    const R uz = vel ? R(vel[2LL * p.N + c]) : R(0.0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fe[i] = R(feq_dev<Q, double>(i, r - 1.0, r, ux, uy, uz));
+    for (int i = 0; i < Q; ++i) fe[i] = feq_dev<Q, R>(i, R(r - 1.0), R(r), ux, uy, uz);
   } else {
     const R ux = vel ? R(vel[c]) : R(0.0);
     const R uy = vel ? R(vel[(long long)p.N + c]) : R(0.0);
@@ -1005,20 +1006,44 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       }
     }
     double rho = collide_any<Q, S, COLL>(f, p, bad);
+    // moments of the stored post-collision PDFs, in post_moments' arithmetic
+    // (new interface cells average them over their neighbours)
+    R mu[3];
     if constexpr (S::kDev) {
       // the density as the stored PDFs hold it (FP64 sum of stored values):
       // the mass a conversion to liquid hands over to the PDFs
       double sd = 0.0;
+      R fs[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const T v = S::stored(f[i]);
         B[(long long)i * Np + c] = v;
-        sd += (double)S::loadd(v);
+        fs[i] = S::loadd(v);
+        sd += (double)fs[i];
       }
       rho = 1.0 + sd;
+      R r0, jx0, jy0, jz0;
+      sums<Q, R>(fs, r0, jx0, jy0, jz0);
+      const R rr = R(rho);
+      mu[0] = jx0 / rr - R(0.5) * R(p.g[0]);
+      mu[1] = jy0 / rr - R(0.5) * R(p.g[1]);
+      mu[2] = jz0 / rr - R(0.5) * R(p.g[2]);
+      d.mom_rho[c] = rho;
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
+      R r0, jx0, jy0, jz0;
+      sums<Q, R>(f, r0, jx0, jy0, jz0);
+      mu[0] = jx0 / r0 - R(0.5) * R(p.g[0]);
+      mu[1] = jy0 / r0 - R(0.5) * R(p.g[1]);
+      mu[2] = jz0 / r0 - R(0.5) * R(p.g[2]);
+      d.mom_rho[c] = (double)r0;
+    }
+    {
+      R* mu_out = (R*)d.mom_u;
+      mu_out[3LL * c + 0] = mu[0];
+      mu_out[3LL * c + 1] = mu[1];
+      mu_out[3LL * c + 2] = mu[2];
     }
     {
       const uint8_t fl = flags[c];
@@ -1064,6 +1089,9 @@ __device__ __forceinline__ void resolve_cell(const DPtrs& d, const KParams& p, i
     d.conv[c] = cv;
     if (cv == CV_NONE) return;
     const int want = (cv == CV_TOL) ? T_GAS : T_LIQ;
+    // claim first, then reserve all of this cell's new entries with one
+    // atomic (the list's order enters no result)
+    unsigned fresh = 0u;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
@@ -1071,8 +1099,13 @@ __device__ __forceinline__ void resolve_cell(const DPtrs& d, const KParams& p, i
       unsigned* word = (unsigned*)(d.claim + (nb & ~3));
       const unsigned bit = 1u << (8 * (nb & 3));
       const unsigned old = atomicOr(word, bit);
-      if (!(old & bit)) d.newlist[atomicAdd(&d.counts[2], 1)] = nb;
+      if (!(old & bit)) fresh |= 1u << i;
     }
+    if (!fresh) return;
+    int pos = atomicAdd(&d.counts[2], __popc(fresh));
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if ((fresh >> i) & 1u) d.newlist[pos++] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
   }
 
 template <int Q>
@@ -1115,6 +1148,13 @@ __device__ __forceinline__ void count_cell(const DPtrs& d, const KParams& p, int
       const double mex = (cv == CV_TOL) ? (m - d.rho_band[k]) : m;
       d.share[c] = mex / (double)nrecv;
       d.cfin[c] = cv;
+      // flag the interface neighbours, which gather this cell's share: the
+      // others skip the gather (it would add nothing)
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+        if (nb >= 0 && (d.flags[nb] & F_TYPE) == T_IFACE) d.rcv[nb] = 1;
+      }
     }
   }
 
@@ -1147,7 +1187,10 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
     const int c = is_band ? band[k] : d.newlist[k - nb_];
     int x, y, z;
     decode(p, c, x, y, z);
+    bool gather = true;
     if (is_band) {
+      gather = d.rcv[c] != 0;
+      if (gather) d.rcv[c] = 0;
       const uint8_t f = d.cfin[c];
       if (f == CV_TOL) {
         d.phi[c] = 1.0;
@@ -1160,11 +1203,15 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
         return;
       }
     }
+    // excess shares of converted neighbours in direction order; an interface
+    // cell that no converted cell flagged has none (s stays 0)
     double s = 0.0;
+    if (gather) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-      if (converted(d, nb)) s = s + d.share[nb];
+      for (int i = 1; i < Q; ++i) {
+        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+        if (converted(d, nb)) s = s + d.share[nb];
+      }
     }
     if (is_band) {
       const double m = d.mass[c] + s;
@@ -1187,7 +1234,15 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
         if (!use) continue;
         double rn;
         R un[3];
-        post_moments<Q, S>(B, Np, nb, p, rn, un);
+        if (nt == T_IFACE) {  // moments cached by the interface kernel
+          const R* mu = (const R*)d.mom_u;
+          rn = d.mom_rho[nb];
+          un[0] = mu[3LL * nb + 0];
+          un[1] = mu[3LL * nb + 1];
+          un[2] = mu[3LL * nb + 2];
+        } else {
+          post_moments<Q, S>(B, Np, nb, p, rn, un);
+        }
         sr = sr + rn;
         sx = sx + (double)un[0];
         sy = sy + (double)un[1];

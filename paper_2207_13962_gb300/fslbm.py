@@ -290,11 +290,13 @@ class Context:
     def set_timing(self, on):
         self._check(self.lib.fslbm_set_timing(self.h, int(bool(on))))
 
+    STAGES = ["geometry", "bulk", "interface", "resolve", "count", "apply", "finalize", "bubbles"]
+
     def stage_times(self):
-        ms = np.zeros(5, np.float64)
+        ms = np.zeros(len(self.STAGES), np.float64)
         n = C.c_int(0)
-        self._check(self.lib.fslbm_stage_times(self.h, _ptr(ms), 5, C.byref(n)))
-        return dict(zip(["geometry", "bulk", "interface", "convert", "bubbles"], ms.tolist())), n.value
+        self._check(self.lib.fslbm_stage_times(self.h, _ptr(ms), len(self.STAGES), C.byref(n)))
+        return dict(zip(self.STAGES, ms.tolist())), n.value
 
     def interface_count(self):
         n = C.c_int64(0)

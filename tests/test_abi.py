@@ -49,3 +49,25 @@ def test_params_default_and_invalid_create_need_no_gpu():
     assert lib.fslbm_create(ctypes.byref(dom), 19, 1, 9, ctypes.byref(p), ctypes.byref(h)) == fslbm.EINVAL
     p.omega = 2.5
     assert lib.fslbm_create(ctypes.byref(dom), 19, 1, 3, ctypes.byref(p), ctypes.byref(h)) == fslbm.EINVAL
+
+
+def test_memory_estimate_needs_no_gpu():
+    """The admission estimate is host arithmetic: it grows with the domain
+    and the stored precision, counts init's velocity staging, and rejects
+    bad sizes and enums."""
+    from paper_2207_13962_gb300 import fslbm
+    lib = fslbm.load()
+    e = {prec: fslbm.memory_estimate((64, 64, 64), 19, prec) for prec in ("FP64", "FP32", "FP16S", "BF16S")}
+    assert e["FP64"] > e["FP32"] > e["FP16S"] == e["BF16S"]
+    N = 64 ** 3
+    # two FP32 PDF buffers alone take 2 * 19 * 4 bytes per cell
+    assert e["FP32"] >= 2 * 19 * 4 * N
+    assert fslbm.memory_estimate((64, 64, 64), 27, "FP32") > e["FP32"]
+    assert fslbm.memory_estimate((64, 64, 64), 19, "FP32", with_velocity=True) == e["FP32"] + 24 * N
+    assert fslbm.memory_estimate((128, 64, 64), 19, "FP32") > 1.9 * e["FP32"]
+    b = ctypes.c_size_t(0)
+    bad = fslbm.fslbm_domain(0, 4, 4, (ctypes.c_int * 3)(0, 0, 0))
+    assert lib.fslbm_memory_estimate(ctypes.byref(bad), 19, 1, 0, ctypes.byref(b)) == fslbm.EINVAL
+    dom = fslbm.fslbm_domain(4, 4, 4, (ctypes.c_int * 3)(0, 0, 0))
+    assert lib.fslbm_memory_estimate(ctypes.byref(dom), 18, 1, 0, ctypes.byref(b)) == fslbm.EINVAL
+    assert lib.fslbm_memory_estimate(ctypes.byref(dom), 19, 7, 0, ctypes.byref(b)) == fslbm.EINVAL

@@ -199,3 +199,20 @@ def test_timing_mode_matches_graph_mode(gpu_lib):
     np.testing.assert_array_equal(ra["pdf"], rb["pdf"])
     times, launches = b.stage_times()
     assert launches == 20 * 7 and times["bulk"] > 0
+
+
+def test_reinit_matches_fresh_context(gpu_lib):
+    """fslbm_init on a context that has already stepped starts a run that is
+    bitwise the run of a fresh context (no state of the earlier run, such as
+    work-list marks, survives)."""
+    from paper_2207_13962_gb300 import fslbm
+    sc = S.random_interface(shape=(37, 21, 11), seed=7)
+    a = fslbm.context_for(sc, precision="FP64")
+    a.step(17)
+    a.init(sc.fill, sc.flags, sc.velocity, sc.density)
+    b = fslbm.context_for(sc, precision="FP64")
+    a.step(25)
+    b.step(25)
+    ra, rb = a.read(), b.read()
+    for k in ("flags", "fill", "mass", "pdf"):
+        np.testing.assert_array_equal(ra[k], rb[k], err_msg=k)
