@@ -129,11 +129,14 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
-KERNEL_SOURCES = ("paper_2207_13962_gb300/csrc/fslbm_kernels.cuh", "paper_2207_13962_gb300/csrc/fslbm_common.cuh")
+# what k_bulk is compiled from: its own header, the cell layer, the common
+# types and the build flags
+KERNEL_SOURCES = tuple("paper_2207_13962_gb300/" + f for f in (
+    "csrc/fslbm_bulk.cuh", "csrc/fslbm_cell.cuh", "csrc/fslbm_common.cuh", "build.py"))
 
 
 def kernel_source_hash() -> str:
-    """SHA-256 of the kernel sources (the ncu traffic applies only to them)."""
+    """SHA-256 of the bulk sweep's sources (the ncu traffic applies only to them)."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:

@@ -1,0 +1,103 @@
+// Bulk sweep of the FSLBM step (arXiv 2207.13962, Sec. 2.1): the pull
+// stream-collide of liquid cells over the liquid segment list.  Kept in its
+// own header so that the recorded DRAM traffic of this kernel is tied to the
+// sources it is built from (this file, the cell layer and the common types).
+#pragma once
+
+#include "fslbm_cell.cuh"
+
+namespace fslbm {
+// ------------------------------------------------------------ bulk sweep
+// Pull stream-collide of liquid cells (Eqs. nm-lbm-streaming, -collision)
+// with bounce-back at obstacles.  Interface and gas cells are skipped.
+//
+// Bounce-back through the obstacle's slot: a fluid cell x whose pull source
+// x - c_i is an obstacle cell writes, besides its own PDFs, f*_ibar(x) into
+// slot i of that obstacle cell.  That slot is pulled by x alone, so the write
+// is race-free, and next step x pulls its bounced-back PDF from the constant
+// offset like any interior cell: the bulk sweep reads at constant offsets
+// except next to a non-periodic domain face (own-slot bounce-back) or across
+// a periodic face (wrapped index), which take the general path.  Every
+// kernel that produces post-collision PDFs of a fluid cell (bulk, interface,
+// new interface cells, init) writes these reflected copies.
+constexpr int kBulkBlock = 256;
+
+// One liquid cell, loads straight from global memory (storage formats of
+// 2 bytes, and batches).
+template <int Q, class S, int COLL>
+__device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int parity, int c,
+                                          uint8_t fl, bool general) {
+  using R = typename S::Real;
+  using T = typename S::T;
+  const T* __restrict__ A = (const T*)d.pdf[parity];
+  T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+  const long long Np = p.Np;
+  R f[Q];
+  if (!general) {
+    const T* Ac = A + c;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(Ac[p.dofs[i]], i);
+  } else {
+    int x, y, z;
+    decode(p, c, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(A[pull_index_general<Q>(p, c, x, y, z, i)], i);
+  }
+  bool bad = false;
+  collide_any<Q, S, COLL>(f, p, bad);
+  T* Bc = B + c;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Bc[(long long)i * Np] = store_w<S, Q>(f[i], i);
+  if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], general, f);
+  if (bad) d.err[0] = 1;
+}
+
+// One warp's share of the direct bulk sweep: groups [w G, w G + G) of the
+// liquid group list, G = 32 / kSegCells (every lane of the warp calls it).
+// Gas lanes that share a 32-byte sector of a PDF slice with a liquid lane
+// store zero PDFs (gas values are never read): the sector is then written
+// whole, which spares HBM a read-modify-write of it.  Interface lanes (the
+// interface kernel writes them concurrently) and obstacle lanes (reflected
+// copies) store nothing.
+#ifndef FSLBM_BULK_FILL
+#define FSLBM_BULK_FILL 1
+#endif
+template <int Q, class S, int COLL>
+__device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int parity, int w,
+                                          int nseg) {
+  using T = typename S::T;
+  using R = typename S::Real;
+  constexpr int kGroups = 32 / kSegCells;
+  constexpr int kFill = (32 / (int)sizeof(T)) < kSegCells ? (32 / (int)sizeof(T)) : kSegCells;
+  const int lane = threadIdx.x & 31;
+  const int e = w * kGroups + lane / kSegCells;
+  const int c = e < nseg ? d.segs[e] * kSegCells + (lane % kSegCells) : p.N;
+  const uint8_t fl = c < p.N ? d.flags[c] : (uint8_t)T_IFACE;
+  const int t = fl & F_TYPE;
+  const bool liq = t == T_LIQ;
+  // the whole warp takes the general path when one of its cells needs it
+  const bool general = __any_sync(0xffffffffu, liq && (fl & (F_FACE | F_WRAP)));
+  const unsigned lm = __ballot_sync(0xffffffffu, liq);
+  if (liq) {
+    bulk_cell<Q, S, COLL>(d, p, parity, c, fl, general);
+  } else if (FSLBM_BULK_FILL) {
+    const unsigned grp = (lm >> (lane & ~(kFill - 1))) & ((1u << kFill) - 1u);
+    if (grp && t == T_GAS) {
+      T* __restrict__ B = (T*)d.pdf[parity ^ 1];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
+    }
+  }
+}
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
+    k_bulk(DPtrs d, KParams p, int parity) {
+  constexpr int kGroups = 32 / kSegCells;
+  const int nseg = d.counts[5];
+  const int warps = (gridDim.x * kBulkBlock) >> 5;
+  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
+    bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
+}
+
+}  // namespace fslbm
