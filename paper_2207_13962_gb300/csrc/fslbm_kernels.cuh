@@ -305,12 +305,17 @@ constexpr int GB = GE * GE * GE;         // 2744 box positions
 constexpr int GS = GT + 4;               // phi~ sub-box edge (12)
 constexpr int GN = GT + 2;               // n^ sub-box edge (10)
 constexpr int kGeoBlock = 256;
+constexpr int kGeoPer = (GB + kGeoBlock - 1) / kGeoBlock;  // box positions per thread
 // geometry blocks per interface-band block: each tile's block runs four
 // dependent shared-memory phases, so many resident tiles hide the latency
 #ifndef FSLBM_GEO_MULT
 #define FSLBM_GEO_MULT 3
 #endif
 constexpr int kGeoGridMult = FSLBM_GEO_MULT;
+#ifndef FSLBM_GEO_MINB
+#define FSLBM_GEO_MINB 1
+#endif
+constexpr int kGeoMinBlocks = FSLBM_GEO_MINB;  // resident geometry blocks per SM compiled for
 
 template <class R>
 constexpr size_t geometry_smem() {
@@ -333,21 +338,35 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
 
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const int ox = tx * GT - 3, oy = ty * GT - 3, oz = tz * GT - 3;
+    // all of a thread's global reads of the box are issued before the first
+    // shared-memory store (kGeoBlock threads, kGeoPer positions each)
     __syncthreads();
-    for (int b = threadIdx.x; b < GB; b += blockDim.x) {
-      const int i = b % GE, j = (b / GE) % GE, k = b / (GE * GE);
-      const int X = wrapc(ox + i, p.nx, p.per[0]);
-      const int Y = wrapc(oy + j, p.ny, p.per[1]);
-      const int Z = wrapc(oz + k, p.nz, p.per[2]);
-      uint8_t t = 4;  // outside the domain: solid
-      R v = R(0.0);
-      if (X >= 0 && Y >= 0 && Z >= 0) {
-        const int c = X + p.nx * (Y + p.ny * Z);
-        t = d.flags[c] & F_TYPE;
-        v = R(d.phi[c]);
+    uint8_t tv[kGeoPer];
+    R pv[kGeoPer];
+#pragma unroll
+    for (int r = 0; r < kGeoPer; ++r) {
+      const int b = threadIdx.x + r * kGeoBlock;
+      tv[r] = 4;  // outside the domain: solid
+      pv[r] = R(0.0);
+      if (b < GB) {
+        const int i = b % GE, j = (b / GE) % GE, k = b / (GE * GE);
+        const int X = wrapc(ox + i, p.nx, p.per[0]);
+        const int Y = wrapc(oy + j, p.ny, p.per[1]);
+        const int Z = wrapc(oz + k, p.nz, p.per[2]);
+        if (X >= 0 && Y >= 0 && Z >= 0) {
+          const int c = X + p.nx * (Y + p.ny * Z);
+          tv[r] = d.flags[c] & F_TYPE;
+          pv[r] = R(d.phi[c]);
+        }
       }
-      styp[b] = t;
-      sphi[b] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < kGeoPer; ++r) {
+      const int b = threadIdx.x + r * kGeoBlock;
+      if (b < GB) {
+        styp[b] = tv[r];
+        sphi[b] = pv[r];
+      }
     }
     __syncthreads();
     // smoothed fill level on the 12^3 sub-box
@@ -463,7 +482,7 @@ __device__ __forceinline__ void reset_step_counts(const DPtrs& d, int parity) {
 }
 
 template <int Q, class S>
-__global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int parity) {
+__global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) k_geometry(DPtrs d, KParams p, int parity) {
   extern __shared__ __align__(16) unsigned char g_smem[];
   if (blockIdx.x == 0 && threadIdx.x == 0) reset_step_counts(d, parity);
   const int ntiles = d.counts[3 + parity];
@@ -472,6 +491,16 @@ __global__ void __launch_bounds__(kGeoBlock) k_geometry(DPtrs d, KParams p, int 
 }
 
 // ------------------------------------------------------- interface update
+// Directions whose neighbour data the mass exchange reads ahead at once, and
+// resident blocks of 128 threads per SM the interface kernels are compiled for.
+#ifndef FSLBM_IFACE_CHUNK
+#define FSLBM_IFACE_CHUNK 9
+#endif
+#ifndef FSLBM_IFACE_MINB
+#define FSLBM_IFACE_MINB 1
+#endif
+constexpr int kIfaceChunk = FSLBM_IFACE_CHUNK;
+constexpr int kIfaceMinBlocks = FSLBM_IFACE_MINB;
 // Pull with the free-surface BC (Eq. nm-fslbm-boundary-condition) on the
 // variant's set R (Sec. 3), mass exchange (Eq. nm-fslbm-mass-flux) with
 // Thuerey's adjustment, fill update phi = m / rho, collision, marks.
@@ -522,36 +551,54 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     const double phic = d.phi[c];
     const int clc = d.cls[c];
     double dm = 0.0;
+    // class and fill level of the interface neighbours, read a chunk of
+    // directions at a time ahead of the (ordered) accumulation
+    constexpr int kChunk = kIfaceChunk;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int ntp = nt[i];
-      if (ntp == T_GAS || ntp == T_OBST) continue;
-      const R a = f[OPP(i)];
-      const R b = fx[i];
-      if constexpr (S::kDev) {
-        const double ad = (double)a, bd = (double)b, w = W<Q, double>(i);
-        if (ntp == T_LIQ) {
-          dm = dm + (ad - bd);
-        } else {
-          const int cln = d.cls[nid[i]];
-          double v;
-          if (clc == cln) v = ad - bd;
-          else if (clc == CL_STD) v = (cln == CL_NF) ? ad + w : -(bd + w);
-          else if (clc == CL_NF) v = -(bd + w);
-          else v = ad + w;
-          dm = dm + 0.5 * (phic + d.phi[nid[i]]) * v;
+    for (int i0 = 1; i0 < Q; i0 += kChunk) {
+      int cl9[kChunk];
+      double ph9[kChunk];
+#pragma unroll
+      for (int a = 0; a < kChunk; ++a) {
+        const int i = i0 + a;
+        if (i < Q && nt[i] == T_IFACE) {
+          cl9[a] = d.cls[nid[i]];
+          ph9[a] = d.phi[nid[i]];
         }
-      } else {
-        if (ntp == T_LIQ) {
-          dm = dm + (double)(a - b);
+      }
+#pragma unroll
+      for (int a = 0; a < kChunk; ++a) {
+        const int i = i0 + a;
+        if (i >= Q) continue;
+        const int ntp = nt[i];
+        if (ntp == T_GAS || ntp == T_OBST) continue;
+        const R fa = f[OPP(i)];
+        const R fb = fx[i];
+        if constexpr (S::kDev) {
+          const double ad = (double)fa, bd = (double)fb, w = W<Q, double>(i);
+          if (ntp == T_LIQ) {
+            dm = dm + (ad - bd);
+          } else {
+            const int cln = cl9[a];
+            double v;
+            if (clc == cln) v = ad - bd;
+            else if (clc == CL_STD) v = (cln == CL_NF) ? ad + w : -(bd + w);
+            else if (clc == CL_NF) v = -(bd + w);
+            else v = ad + w;
+            dm = dm + 0.5 * (phic + ph9[a]) * v;
+          }
         } else {
-          const int cln = d.cls[nid[i]];
-          R v;
-          if (clc == cln) v = a - b;
-          else if (clc == CL_STD) v = (cln == CL_NF) ? a : -b;
-          else if (clc == CL_NF) v = -b;
-          else v = a;
-          dm = dm + 0.5 * (phic + d.phi[nid[i]]) * (double)v;
+          if (ntp == T_LIQ) {
+            dm = dm + (double)(fa - fb);
+          } else {
+            const int cln = cl9[a];
+            R v;
+            if (clc == cln) v = fa - fb;
+            else if (clc == CL_STD) v = (cln == CL_NF) ? fa : -fb;
+            else if (clc == CL_NF) v = -fb;
+            else v = fa;
+            dm = dm + 0.5 * (phic + ph9[a]) * (double)v;
+          }
         }
       }
     }
@@ -636,7 +683,7 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
   }
 
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parity) {
+__global__ void __launch_bounds__(128, kIfaceMinBlocks) k_interface(DPtrs d, KParams p, int parity) {
   const int n = d.counts[parity];
   bool bad = false;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
@@ -645,47 +692,72 @@ __global__ void __launch_bounds__(128) k_interface(DPtrs d, KParams p, int parit
 }
 
 // -------------------------------------------------------------- conversion
+// These passes are chains of dependent neighbour reads over a few hundred
+// converting cells, so their duration is the number of round trips to
+// memory along the longest chain.  Each pass reads the neighbours' values
+// one level at a time for all directions together (types, then the values
+// the types select, then the values those select) and writes only after
+// the last read; the arithmetic and its order are those of a per-direction
+// loop.
+
+// Neighbour indices of (x, y, z) and their types (T_OBST outside the domain).
+template <int Q>
+__device__ __forceinline__ void neighbour_types(const DPtrs& d, const KParams& p, int x, int y,
+                                                int z, int* nid, uint8_t* nt) {
+#pragma unroll
+  for (int i = 1; i < Q; ++i) nid[i] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+#pragma unroll
+  for (int i = 1; i < Q; ++i) nt[i] = nid[i] >= 0 ? (uint8_t)(d.flags[nid[i]] & F_TYPE) : (uint8_t)T_OBST;
+}
+
 // Commit m, phi; conflict rule (a cell marked for gas stays interface next
 // to a cell marked for liquid); claim gas neighbours of cells turning liquid
 // and liquid neighbours of cells turning gas as new interface cells.
 template <int Q>
 __device__ __forceinline__ void resolve_cell(const DPtrs& d, const KParams& p, int parity, int k) {
-  const int* __restrict__ band = d.band[parity];
-
-    const int c = band[k];
-    d.mass[c] = d.m_next[k];
-    d.phi[c] = d.phi_next[k];
-    int x, y, z;
-    decode(p, c, x, y, z);
-    uint8_t cv = d.mark[c];
-    if (cv == CV_TOG) {
+  const int c = d.band[parity][k];
+  uint8_t cv = d.mark[c];
+  d.mass[c] = d.m_next[k];
+  d.phi[c] = d.phi_next[k];
+  if (cv == CV_NONE) {
+    d.conv[c] = CV_NONE;
+    return;
+  }
+  int x, y, z;
+  decode(p, c, x, y, z);
+  int nid[Q];
+  uint8_t nt[Q];
+  neighbour_types<Q>(d, p, x, y, z, nid, nt);
+  if (cv == CV_TOG) {
+    uint8_t mk[Q];
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-        if (nb >= 0 && (d.flags[nb] & F_TYPE) == T_IFACE && d.mark[nb] == CV_TOL) cv = CV_NONE;
-      }
-    }
-    d.conv[c] = cv;
-    if (cv == CV_NONE) return;
-    const int want = (cv == CV_TOL) ? T_GAS : T_LIQ;
-    // claim first, then reserve all of this cell's new entries with one
-    // atomic (the list's order enters no result)
-    unsigned fresh = 0u;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-      if (nb < 0 || (d.flags[nb] & F_TYPE) != want) continue;
-      unsigned* word = (unsigned*)(d.claim + (nb & ~3));
-      const unsigned bit = 1u << (8 * (nb & 3));
-      const unsigned old = atomicOr(word, bit);
-      if (!(old & bit)) fresh |= 1u << i;
-    }
-    if (!fresh) return;
-    int pos = atomicAdd(&d.counts[2], __popc(fresh));
+    for (int i = 1; i < Q; ++i) mk[i] = nt[i] == T_IFACE ? d.mark[nid[i]] : (uint8_t)CV_NONE;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-      if ((fresh >> i) & 1u) d.newlist[pos++] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+      if (mk[i] == CV_TOL) cv = CV_NONE;
   }
+  d.conv[c] = cv;
+  if (cv == CV_NONE) return;
+  const int want = (cv == CV_TOL) ? T_GAS : T_LIQ;
+  // claim first (the atomics are independent of one another), then reserve
+  // all of this cell's new entries with one atomic (the list's order enters
+  // no result)
+  unsigned fresh = 0u;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (nt[i] != want) continue;
+    const int nb = nid[i];
+    unsigned* word = (unsigned*)(d.claim + (nb & ~3));
+    const unsigned bit = 1u << (8 * (nb & 3));
+    const unsigned old = atomicOr(word, bit);
+    if (!(old & bit)) fresh |= 1u << i;
+  }
+  if (!fresh) return;
+  int pos = atomicAdd(&d.counts[2], __popc(fresh));
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    if ((fresh >> i) & 1u) d.newlist[pos++] = nid[i];
+}
 
 template <int Q>
 __global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int parity) {
@@ -694,48 +766,48 @@ __global__ void __launch_bounds__(kBlock) k_resolve(DPtrs d, KParams p, int pari
     resolve_cell<Q>(d, p, parity, k);
 }
 
-// flag of a neighbour after conversion, before deferral
-__device__ __forceinline__ bool post_iface(const DPtrs& d, int nb) {
-  if (nb < 0) return false;
-  const int t = d.flags[nb] & F_TYPE;
-  if (t == T_IFACE) return d.conv[nb] == CV_NONE;
-  if (t == T_GAS || t == T_LIQ) return d.claim[nb] != 0;
-  return false;
-}
-
 // Excess-mass receivers (Eq. nm-fslbm-excess-mass): interface cells after
-// conversion in the lattice neighbourhood; none -> the conversion is deferred.
+// conversion in the lattice neighbourhood (interface cells that do not
+// convert, and the gas or liquid cells that conversion claims); none -> the
+// conversion is deferred.
 template <int Q>
 __device__ __forceinline__ void count_cell(const DPtrs& d, const KParams& p, int parity, int k) {
-  const int* __restrict__ band = d.band[parity];
-
-    const int c = band[k];
-    const uint8_t cv = d.conv[c];
-    if (cv == CV_NONE) {
-      d.cfin[c] = CV_NONE;
-      return;
-    }
-    int x, y, z;
-    decode(p, c, x, y, z);
-    int nrecv = 0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) nrecv += post_iface(d, nbr(p, x, y, z, CX(i), CY(i), CZ(i))) ? 1 : 0;
-    if (nrecv == 0) {
-      d.cfin[c] = CV_DEFER;
-    } else {
-      const double m = d.mass[c];
-      const double mex = (cv == CV_TOL) ? (m - d.rho_band[k]) : m;
-      d.share[c] = mex / (double)nrecv;
-      d.cfin[c] = cv;
-      // flag the interface neighbours, which gather this cell's share: the
-      // others skip the gather (it would add nothing)
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-        if (nb >= 0 && (d.flags[nb] & F_TYPE) == T_IFACE) d.rcv[nb] = 1;
-      }
-    }
+  const int c = d.band[parity][k];
+  const uint8_t cv = d.conv[c];
+  if (cv == CV_NONE) {
+    d.cfin[c] = CV_NONE;
+    return;
   }
+  const double m = d.mass[c];
+  const double rb = d.rho_band[k];
+  int x, y, z;
+  decode(p, c, x, y, z);
+  int nid[Q];
+  uint8_t nt[Q];
+  neighbour_types<Q>(d, p, x, y, z, nid, nt);
+  uint8_t nv[Q];  // conv of interface neighbours, claim of gas and liquid ones
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    nv[i] = nt[i] == T_IFACE ? d.conv[nid[i]] : nt[i] != T_OBST ? d.claim[nid[i]] : (uint8_t)0;
+  int nrecv = 0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const bool post = nt[i] == T_IFACE ? nv[i] == CV_NONE : nt[i] != T_OBST && nv[i] != 0;
+    nrecv += post ? 1 : 0;
+  }
+  if (nrecv == 0) {
+    d.cfin[c] = CV_DEFER;
+    return;
+  }
+  const double mex = (cv == CV_TOL) ? (m - rb) : m;
+  d.share[c] = mex / (double)nrecv;
+  d.cfin[c] = cv;
+  // flag the interface neighbours, which gather this cell's share: the
+  // others skip the gather (it would add nothing)
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    if (nt[i] == T_IFACE) d.rcv[nid[i]] = 1;
+}
 
 template <int Q>
 __global__ void __launch_bounds__(kBlock) k_count(DPtrs d, KParams p, int parity) {
@@ -744,10 +816,23 @@ __global__ void __launch_bounds__(kBlock) k_count(DPtrs d, KParams p, int parity
     count_cell<Q>(d, p, parity, k);
 }
 
-__device__ __forceinline__ bool converted(const DPtrs& d, int nb) {
-  if (nb < 0 || (d.flags[nb] & F_TYPE) != T_IFACE) return false;
-  const uint8_t f = d.cfin[nb];
-  return f == CV_TOL || f == CV_TOG;
+__device__ __forceinline__ bool is_converted(uint8_t f) { return f == CV_TOL || f == CV_TOG; }
+
+// 2-bit fields per direction (types T_*, conversion states CV_*)
+__device__ __forceinline__ int field2(uint64_t m, int i) { return (int)((m >> (2 * i)) & 3u); }
+
+// Sum of the excess shares of converted neighbours, in direction order.
+// cfm: 2-bit cfin of the interface neighbours (CV_NONE elsewhere).
+template <int Q>
+__device__ __forceinline__ double gather_shares(const DPtrs& d, const int* nid, uint64_t cfm) {
+  double sh[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) sh[i] = is_converted((uint8_t)field2(cfm, i)) ? d.share[nid[i]] : 0.0;
+  double s = 0.0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    if (is_converted((uint8_t)field2(cfm, i))) s = s + sh[i];
+  return s;
 }
 
 // Excess gather for all interface cells after conversion; PDFs of new
@@ -757,118 +842,155 @@ template <int Q, class S>
 __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int parity, int k) {
   using R = typename S::Real;
   using T = typename S::T;
-  const int* __restrict__ band = d.band[parity];
   const int nb_ = d.counts[parity];
   T* __restrict__ B = (T*)d.pdf[parity ^ 1];
   const long long Np = p.Np;
 
-    const bool is_band = k < nb_;
-    const int c = is_band ? band[k] : d.newlist[k - nb_];
-    int x, y, z;
-    decode(p, c, x, y, z);
-    bool gather = true;
-    if (is_band) {
-      gather = d.rcv[c] != 0;
-      if (gather) d.rcv[c] = 0;
-      const uint8_t f = d.cfin[c];
-      if (f == CV_TOL) {
-        d.phi[c] = 1.0;
-        d.mass[c] = d.rho_band[k];
-        return;
-      }
-      if (f == CV_TOG) {
-        d.phi[c] = 0.0;
-        d.mass[c] = 0.0;
-        return;
-      }
-    }
-    // excess shares of converted neighbours in direction order; an interface
-    // cell that no converted cell flagged has none (s stays 0)
-    double s = 0.0;
-    if (gather) {
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-        if (converted(d, nb)) s = s + d.share[nb];
-      }
-    }
-    if (is_band) {
-      const double m = d.mass[c] + s;
-      d.mass[c] = m;
-      d.phi[c] = m / d.rho_band[k];
+  const bool is_band = k < nb_;
+  const int c = is_band ? d.band[parity][k] : d.newlist[k - nb_];
+  int x, y, z;
+  int nid[Q];
+  if (is_band) {
+    const bool gather = d.rcv[c] != 0;
+    const uint8_t f = d.cfin[c];
+    if (gather) d.rcv[c] = 0;
+    if (f == CV_TOL) {
+      d.phi[c] = 1.0;
+      d.mass[c] = d.rho_band[k];
       return;
     }
-    const int t = d.flags[c] & F_TYPE;
-    if (t == T_GAS) {
-      double sr = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-      int cnt = 0;
+    if (f == CV_TOG) {
+      d.phi[c] = 0.0;
+      d.mass[c] = 0.0;
+      return;
+    }
+    const double m0 = d.mass[c];
+    const double rb = d.rho_band[k];
+    // an interface cell that no converted cell flagged receives nothing
+    double s = 0.0;
+    if (gather) {
+      decode(p, c, x, y, z);
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-        if (nb < 0) continue;
-        const int nt = d.flags[nb] & F_TYPE;
-        bool use = false;
-        if (nt == T_IFACE) use = d.cfin[nb] != CV_TOG;   // stays interface or turns liquid
-        if (nt == T_LIQ) use = d.claim[nb] == 0;         // stays liquid
-        if (!use) continue;
-        double rn;
-        R un[3];
-        if (nt == T_IFACE) {  // moments cached by the interface kernel
+      for (int i = 1; i < Q; ++i) nid[i] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+      unsigned ifm = 0u;  // interface neighbours
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if (nid[i] >= 0 && (d.flags[nid[i]] & F_TYPE) == T_IFACE) ifm |= 1u << i;
+      uint64_t cfm = 0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if ((ifm >> i) & 1u) cfm |= (uint64_t)(d.cfin[nid[i]] & 3u) << (2 * i);
+      s = gather_shares<Q>(d, nid, cfm);
+    }
+    const double m = m0 + s;
+    d.mass[c] = m;
+    d.phi[c] = m / rb;
+    return;
+  }
+
+  // a new interface cell (gas or liquid before this step)
+  const uint8_t fl = d.flags[c];
+  const int t = fl & F_TYPE;
+  decode(p, c, x, y, z);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) nid[i] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+  uint64_t ntm = 0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    ntm |= (uint64_t)(nid[i] >= 0 ? (d.flags[nid[i]] & F_TYPE) : T_OBST) << (2 * i);
+  uint64_t cfm = 0;   // cfin of interface neighbours
+  uint32_t clm = 0u;  // claimed gas or liquid neighbours
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int nt = field2(ntm, i);
+    if (nt == T_IFACE) cfm |= (uint64_t)(d.cfin[nid[i]] & 3u) << (2 * i);
+    if ((nt == T_GAS || nt == T_LIQ) && d.claim[nid[i]] != 0) clm |= 1u << i;
+  }
+  const double s = gather_shares<Q>(d, nid, cfm);
+  if (t == T_GAS) {
+    // neighbours that stay or turn liquid, or stay interface
+    unsigned use = 0u;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int nt = field2(ntm, i);
+      if (nt == T_IFACE && field2(cfm, i) != CV_TOG) use |= 1u << i;
+      if (nt == T_LIQ && !((clm >> i) & 1u)) use |= 1u << i;
+    }
+    double sr = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    int cnt = 0;
+    // moments cached by the interface kernel, read a few directions at a
+    // time; liquid neighbours (none next to a gas cell while the interface
+    // layer is closed) form theirs from the stored PDFs
+    constexpr int kChunk = 5;
+#pragma unroll
+    for (int i0 = 1; i0 < Q; i0 += kChunk) {
+      double rn[kChunk];
+      R un[kChunk][3];
+#pragma unroll
+      for (int a = 0; a < kChunk; ++a) {
+        const int i = i0 + a;
+        if (i < Q && ((use >> i) & 1u) && field2(ntm, i) == T_IFACE) {
           const R* mu = (const R*)d.mom_u;
-          rn = d.mom_rho[nb];
-          un[0] = mu[3LL * nb + 0];
-          un[1] = mu[3LL * nb + 1];
-          un[2] = mu[3LL * nb + 2];
-        } else {
-          post_moments<Q, S>(B, Np, nb, p, rn, un);
+          rn[a] = d.mom_rho[nid[i]];
+          un[a][0] = mu[3LL * nid[i] + 0];
+          un[a][1] = mu[3LL * nid[i] + 1];
+          un[a][2] = mu[3LL * nid[i] + 2];
         }
-        sr = sr + rn;
-        sx = sx + (double)un[0];
-        sy = sy + (double)un[1];
-        sz = sz + (double)un[2];
+      }
+#pragma unroll
+      for (int a = 0; a < kChunk; ++a) {
+        const int i = i0 + a;
+        if (i >= Q || !((use >> i) & 1u)) continue;
+        if (field2(ntm, i) != T_IFACE) post_moments<Q, S>(B, Np, nid[i], p, rn[a], un[a]);
+        sr = sr + rn[a];
+        sx = sx + (double)un[a][0];
+        sy = sy + (double)un[a][1];
+        sz = sz + (double)un[a][2];
         ++cnt;
       }
-      double rb = 1.0, ub0 = 0.0, ub1 = 0.0, ub2 = 0.0;
-      if (cnt > 0) {
-        rb = sr / (double)cnt;
-        ub0 = sx / (double)cnt;
-        ub1 = sy / (double)cnt;
-        ub2 = sz / (double)cnt;
-      }
-      R fn[Q];
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if constexpr (S::kDev)
-          fn[i] = feq_dev<Q, R>(i, R(rb - 1.0), R(rb), R(ub0), R(ub1), R(ub2));
-        else
-          fn[i] = feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2));
-        B[(long long)i * Np + c] = store_w<S, Q>(fn[i], i);
-      }
-      const uint8_t fl = d.flags[c];
-      if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], (fl & F_WRAP) != 0, fn);
-      const double m = 0.0 + s;
-      d.mass[c] = m;
-      d.phi[c] = m / rb;
-    } else {  // from liquid
-      double rn;
-      R un[3];
-      post_moments<Q, S>(B, Np, c, p, rn, un);
-      const double m = rn + s;
-      d.mass[c] = m;
-      d.phi[c] = m / rn;
-      int best = -1;
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int nb = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-        if (nb < 0) continue;
-        const int nt = d.flags[nb] & F_TYPE;
-        const bool gas_after = (nt == T_GAS && d.claim[nb] == 0) || (nt == T_IFACE && d.cfin[nb] == CV_TOG);
-        const int bb = d.bid[nb];
-        if (gas_after && bb >= 0 && (best < 0 || bb < best)) best = bb;
-      }
-      d.bid[c] = best;
     }
+    double rb = 1.0, ub0 = 0.0, ub1 = 0.0, ub2 = 0.0;
+    if (cnt > 0) {
+      rb = sr / (double)cnt;
+      ub0 = sx / (double)cnt;
+      ub1 = sy / (double)cnt;
+      ub2 = sz / (double)cnt;
+    }
+    const uint32_t wm = (fl & F_NEAR_WALL) ? d.wallmask[c] : 0u;
+    R fn[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (S::kDev)
+        fn[i] = feq_dev<Q, R>(i, R(rb - 1.0), R(rb), R(ub0), R(ub1), R(ub2));
+      else
+        fn[i] = feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2));
+      B[(long long)i * Np + c] = store_w<S, Q>(fn[i], i);
+    }
+    if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, wm, (fl & F_WRAP) != 0, fn);
+    const double m = 0.0 + s;
+    d.mass[c] = m;
+    d.phi[c] = m / rb;
+  } else {  // from liquid
+    int bb[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int nt = field2(ntm, i);
+      const bool gas_after = (nt == T_GAS && !((clm >> i) & 1u)) || (nt == T_IFACE && field2(cfm, i) == CV_TOG);
+      bb[i] = gas_after ? d.bid[nid[i]] : -1;
+    }
+    double rn;
+    R un[3];
+    post_moments<Q, S>(B, Np, c, p, rn, un);
+    int best = -1;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (bb[i] >= 0 && (best < 0 || bb[i] < best)) best = bb[i];
+    const double m = rn + s;
+    d.mass[c] = m;
+    d.phi[c] = m / rn;
+    d.bid[c] = best;
   }
+}
 
 template <int Q, class S>
 __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
@@ -1143,7 +1265,7 @@ static __global__ void kb_plan_back(DomRec* recs, BatchPlan pl) {
 }
 
 template <int Q, class S>
-__global__ void __launch_bounds__(kGeoBlock) kb_geometry(const DomRec* __restrict__ recs, BatchPlan pl) {
+__global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) kb_geometry(const DomRec* __restrict__ recs, BatchPlan pl) {
   extern __shared__ __align__(16) unsigned char g_smem[];
   const int total = pl.tiles[pl.n];
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -1166,7 +1288,7 @@ __global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? k
 }
 
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
+__global__ void __launch_bounds__(128, kIfaceMinBlocks) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
   const int total = pl.band[pl.n];
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     const int k = find_domain(pl.band, pl.n, g);
