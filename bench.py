@@ -582,6 +582,47 @@ def bench_reference(args, ws, rank):
     return line
 
 
+def sector_census(workload: str, variant: str = "OM") -> dict:
+    """Host-side count of the 32-byte sectors the bulk sweep reads and writes
+    on a workload's initial flag field (FP32 storage, D3Q19 or D3Q27): the
+    figures that DRAM counters of k_bulk are compared with.  No GPU."""
+    import numpy as np
+    from paper_2207_13962_gb300 import scenarios as S
+    sc, _ = make_workload(workload, variant)
+    nx, ny, nz = sc.shape
+    N = nx * ny * nz
+    fl = np.asarray(sc.flags).reshape(-1)
+    lin = np.flatnonzero(fl == S.LIQ)
+    x, y, z = lin % nx, (lin // nx) % ny, lin // (nx * ny)
+    dirs = [(a, b, c) for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1)
+            if sc.q == 27 or abs(a) + abs(b) + abs(c) <= 2]
+    seg = lin // 32
+    out = {"liquid_cells": int(lin.size), "segments": int(np.unique(seg).size)}
+    out["lane_occupancy"] = lin.size / (32.0 * out["segments"])
+    distinct = pairs = d64 = d128 = refl = 0
+    obst = fl == S.OBST
+    for (cx, cy, cz) in dirs:
+        src = (x - cx) + nx * ((y - cy) + ny * (z - cz))
+        distinct += np.unique(src // 8).size
+        pairs += np.unique(seg.astype(np.int64) * (N // 8 + 2) + src // 8).size
+        d64 += np.unique(src // 16).size
+        d128 += np.unique(src // 32).size
+        if (cx, cy, cz) != (0, 0, 0):
+            X, Y, Z = x - cx, y - cy, z - cz
+            ok = (X >= 0) & (X < nx) & (Y >= 0) & (Y < ny) & (Z >= 0) & (Z < nz)
+            tgt = X[ok] + nx * (Y[ok] + ny * Z[ok])
+            refl += np.unique(tgt[obst[tgt]] // 8).size
+    nsec = (N + 7) // 8
+    pad = lambda m: np.concatenate([m, np.zeros(nsec * 8 - N, bool)]).reshape(nsec, 8)
+    has_l = pad(fl == S.LIQ).any(1)
+    part = has_l & (pad(obst).any(1) | pad(fl == S.IFACE).any(1))
+    out.update(algorithmic_read_MB=lin.size * len(dirs) * 4 / 1e6,
+               distinct_read_sectors=int(distinct), warp_sector_requests=int(pairs),
+               read_sectors_64B_chunks=int(d64 * 2), read_sectors_128B_lines=int(d128 * 4),
+               partial_write_sectors=int(part.sum()) * len(dirs), reflected_write_sectors=int(refl))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -594,6 +635,8 @@ def main(argv=None):
     ap.add_argument("--variant", default="OM", choices=["NBRC", "NBKC", "OM", "OM3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--sector-census", action="store_true",
+                    help="print the bulk sweep's sector counts on the workload's initial state (CPU only)")
     ap.add_argument("--batch-n", type=int, default=64, help="batch_cylinders: domains")
     ap.add_argument("--batch-steps", type=int, default=200, help="batch_cylinders: timed steps")
     ap.add_argument("--batch-precision", default="FP16S", choices=["FP16S", "BF16S", "FP32"])
@@ -603,6 +646,9 @@ def main(argv=None):
     ap.add_argument("--max-active", type=int, default=16, help="serve_drops: resident runs")
     ap.add_argument("--chunk-steps", type=int, default=100, help="serve_drops: steps per round")
     args = ap.parse_args(argv)
+    if args.sector_census:
+        print(json.dumps(sector_census(args.workload, args.variant)))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     ws, rank, local = dist_env()

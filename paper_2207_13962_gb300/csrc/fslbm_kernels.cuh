@@ -304,7 +304,7 @@ constexpr int GE = GT + 6;               // box edge with halo 3
 constexpr int GB = GE * GE * GE;         // 2744 box positions
 constexpr int GS = GT + 4;               // phi~ sub-box edge (12)
 constexpr int GN = GT + 2;               // n^ sub-box edge (10)
-constexpr int kGeoBlock = 256;
+constexpr int kGeoBlock = 192;  // the z-column phases use 144 and 100 threads
 constexpr int kGeoPer = (GB + kGeoBlock - 1) / kGeoBlock;  // box positions per thread
 // geometry blocks per interface-band block: each tile's block runs four
 // dependent shared-memory phases, so many resident tiles hide the latency
@@ -313,9 +313,16 @@ constexpr int kGeoPer = (GB + kGeoBlock - 1) / kGeoBlock;  // box positions per 
 #endif
 constexpr int kGeoGridMult = FSLBM_GEO_MULT;
 #ifndef FSLBM_GEO_MINB
-#define FSLBM_GEO_MINB 1
+#define FSLBM_GEO_MINB 3
 #endif
 constexpr int kGeoMinBlocks = FSLBM_GEO_MINB;  // resident geometry blocks per SM compiled for
+
+// Fill level stored for obstacle and out-of-domain box positions: stencils
+// substitute their centre's value there (no fill level comes near it).
+template <class R>
+__device__ __forceinline__ R kObstacle() { return R(-1.0e30); }
+template <class R>
+__device__ __forceinline__ bool is_obstacle(R v) { return v < R(-1.0e29); }
 
 template <class R>
 constexpr size_t geometry_smem() {
@@ -365,67 +372,95 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
       const int b = threadIdx.x + r * kGeoBlock;
       if (b < GB) {
         styp[b] = tv[r];
-        sphi[b] = pv[r];
+        sphi[b] = tv[r] >= T_OBST ? kObstacle<R>() : pv[r];
       }
     }
     __syncthreads();
-    // smoothed fill level on the 12^3 sub-box
-    for (int s = threadIdx.x; s < GS * GS * GS; s += blockDim.x) {
-      const int i = s % GS + 1, j = (s / GS) % GS + 1, k = s / (GS * GS) + 1;
-      const int b = i + GE * (j + GE * k);
-      if (styp[b] >= T_OBST) {
-        sps[s] = R(0.0);
-        continue;
-      }
-      const R pc = sphi[b];
-      R acc = R(0.0);
+    // smoothed fill level on the 12^3 sub-box: one thread per z-column,
+    // the 3x3x3 window slides along z in registers
+    if (threadIdx.x < GS * GS) {
+      const int i = threadIdx.x % GS + 1, j = threadIdx.x / GS + 1;
+      R w[3][9];  // planes k-1, k, k+1 of the window, (dy, dx) row-major
 #pragma unroll
-      for (int dz = -1; dz <= 1; ++dz)
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
+        for (int e = 0; e < 9; ++e)
+          w[q + 1][e] = sphi[(i + e % 3 - 1) + GE * ((j + e / 3 - 1) + GE * q)];
+      for (int k = 1; k <= GS; ++k) {
 #pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int nb = b + dx + GE * (dy + GE * dz);
-            const R v = (styp[nb] >= T_OBST) ? pc : sphi[nb];
-            acc = acc + k8w<R>(dx * dx + dy * dy + dz * dz) * v;
-          }
-      sps[s] = acc / wsum;
-    }
-    __syncthreads();
-    // Parker-Youngs normal on the 10^3 sub-box
-    for (int s = threadIdx.x; s < GN * GN * GN; s += blockDim.x) {
-      const int i = s % GN + 2, j = (s / GN) % GN + 2, k = s / (GN * GN) + 2;
-      const int b = i + GE * (j + GE * k);
-      R out[3] = {R(0.0), R(0.0), R(0.0)};
-      if (styp[b] < T_OBST) {
-        auto psi = [&](int ii, int jj, int kk) { return sps[(ii - 1) + GS * ((jj - 1) + GS * (kk - 1))]; };
-        const R pc = psi(i, j, k);
-        R nn[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
+        for (int e = 0; e < 9; ++e) {
+          w[0][e] = w[1][e];
+          w[1][e] = w[2][e];
+          w[2][e] = sphi[(i + e % 3 - 1) + GE * ((j + e / 3 - 1) + GE * (k + 1))];
+        }
+        const R pc = w[1][4];
+        R out = kObstacle<R>();
+        if (!is_obstacle(pc)) {
           R acc = R(0.0);
 #pragma unroll
-          for (int pp = -1; pp <= 1; ++pp)
+          for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-            for (int r = -1; r <= 1; ++r) {
-              const int ax = (a == 0) ? 1 : r, ay = (a == 0) ? r : (a == 1) ? 1 : pp,
-                        az = (a == 2) ? 1 : pp;
-              const int bx = (a == 0) ? -1 : ax, by = (a == 1) ? -1 : ay, bz = (a == 2) ? -1 : az;
-              const int b1 = b + ax + GE * (ay + GE * az), b2 = b + bx + GE * (by + GE * bz);
-              const R vp = (styp[b1] >= T_OBST) ? pc : psi(i + ax, j + ay, k + az);
-              const R vm = (styp[b2] >= T_OBST) ? pc : psi(i + bx, j + by, k + bz);
-              const R w = (pp == 0 && r == 0) ? R(4.0) : (pp == 0 || r == 0) ? R(2.0) : R(1.0);
-              acc = acc + w * (vp - vm);
-            }
-          nn[a] = acc;
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+              for (int dx = -1; dx <= 1; ++dx) {
+                const R raw = w[dz + 1][(dy + 1) * 3 + dx + 1];
+                const R v = is_obstacle(raw) ? pc : raw;
+                acc = acc + k8w<R>(dx * dx + dy * dy + dz * dz) * v;
+              }
+          out = acc / wsum;
         }
-        const R len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) out[a] = (len > R(0.0)) ? nn[a] / len : R(0.0);
+        sps[(i - 1) + GS * ((j - 1) + GS * (k - 1))] = out;
       }
-      snh[s] = out[0];
-      snh[GN * GN * GN + s] = out[1];
-      snh[2 * GN * GN * GN + s] = out[2];
+    }
+    __syncthreads();
+    // Parker-Youngs normal on the 10^3 sub-box, z-columns as above
+    if (threadIdx.x < GN * GN) {
+      const int i = threadIdx.x % GN + 2, j = threadIdx.x / GN + 2;
+      auto psi = [&](int ii, int jj, int kk) { return sps[(ii - 1) + GS * ((jj - 1) + GS * (kk - 1))]; };
+      R w[3][9];
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) w[q + 1][e] = psi(i + e % 3 - 1, j + e / 3 - 1, 1 + q);
+      for (int k = 2; k < 2 + GN; ++k) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          w[0][e] = w[1][e];
+          w[1][e] = w[2][e];
+          w[2][e] = psi(i + e % 3 - 1, j + e / 3 - 1, k + 1);
+        }
+        auto at = [&](int dx, int dy, int dz) { return w[dz + 1][(dy + 1) * 3 + dx + 1]; };
+        const R pc = at(0, 0, 0);
+        R out[3] = {R(0.0), R(0.0), R(0.0)};
+        if (!is_obstacle(pc)) {
+          R nn[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            R acc = R(0.0);
+#pragma unroll
+            for (int pp = -1; pp <= 1; ++pp)
+#pragma unroll
+              for (int r = -1; r <= 1; ++r) {
+                const int ax = (a == 0) ? 1 : r, ay = (a == 0) ? r : (a == 1) ? 1 : pp,
+                          az = (a == 2) ? 1 : pp;
+                const int bx = (a == 0) ? -1 : ax, by = (a == 1) ? -1 : ay, bz = (a == 2) ? -1 : az;
+                const R rp = at(ax, ay, az), rm = at(bx, by, bz);
+                const R vp = is_obstacle(rp) ? pc : rp;
+                const R vm = is_obstacle(rm) ? pc : rm;
+                const R wt = (pp == 0 && r == 0) ? R(4.0) : (pp == 0 || r == 0) ? R(2.0) : R(1.0);
+                acc = acc + wt * (vp - vm);
+              }
+            nn[a] = acc;
+          }
+          const R len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) out[a] = (len > R(0.0)) ? nn[a] / len : R(0.0);
+        }
+        const int s3 = (i - 2) + GN * ((j - 2) + GN * (k - 2));
+        snh[s3] = out[0];
+        snh[GN * GN * GN + s3] = out[1];
+        snh[2 * GN * GN * GN + s3] = out[2];
+      }
     }
     __syncthreads();
     // curvature, gas density and Thuerey class of the tile's interface cells
