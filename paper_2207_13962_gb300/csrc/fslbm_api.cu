@@ -213,7 +213,17 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   c->band_grid = sms * 2;
   // the persistent bulk sweep leaves FSLBM_BULK_RESERVE block slots per SM to
   // the interface-band kernels that run beside it
-  c->bulk_grid = sms * (c->ops.bulk_blocks_per_sm - FSLBM_BULK_RESERVE);
+  // (and never more blocks than can be resident at once: the sweep's work
+  // is split statically over its blocks)
+  int bulk_per_sm = c->ops.bulk_blocks_per_sm - FSLBM_BULK_RESERVE;
+  {
+    int fit = 0;
+    const void* fn = c->ops.bulk_fn[k.collision == 0 ? 0 : 1];
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kBulkBlock, c->ops.bulk_smem) == cudaSuccess &&
+        fit > 0 && fit < bulk_per_sm)
+      bulk_per_sm = fit;
+  }
+  c->bulk_grid = sms * bulk_per_sm;
 
   DPtrs& d = c->d;
   std::memset(&d, 0, sizeof(d));
@@ -225,7 +235,9 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   if (e == cudaSuccess) e = dalloc(c, &(ptr), (bytes));
   ALLOC(d.pdf[0], pdf_bytes);
   ALLOC(d.pdf[1], pdf_bytes);
-  ALLOC(d.flags, n4);
+  // flags padded to whole 32-byte segments (the TMA bulk sweep copies them)
+  const size_t n32 = (size_t)((N + 31) / 32 * 32);
+  ALLOC(d.flags, n32);
   ALLOC(d.wallmask, N * sizeof(uint32_t));
   ALLOC(d.phi, N * sizeof(double));
   ALLOC(d.mass, N * sizeof(double));
@@ -295,7 +307,7 @@ fslbm_status fslbm_memory_estimate(const fslbm_domain* domain, fslbm_lattice lat
       (size_t)((domain->nx + 7) / 8) * ((domain->ny + 7) / 8) * ((domain->nz + 7) / 8);
   const size_t nseg = (N + kSegCells - 1) / kSegCells;
   size_t b = 2 * (size_t)lattice * Np * elem;            // PDFs, two buffers
-  b += 7 * n4;                                           // flags, cls, mark, conv, cfin, claim, rcv
+  b += 6 * n4 + (N + 31) / 32 * 32;                      // cls, mark, conv, cfin, claim, rcv; flags
   b += N * (4 + 8 + 8 + 4 + 8 + 4 + 4 + 4);              // wallmask phi mass bid share band[2] newlist
   b += N * (7 * rs + 4 * 8);                             // nhat rhog mom m_next phi_next rho_band
   b += 3 * ntiles * 4 + 2 * nseg * 4 + 4096;             // tiles, segments, counters, partials
@@ -494,6 +506,7 @@ fslbm_status fslbm_sync(fslbm_ctx* c) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_sync");
   if (herr[0]) return fail(c, FSLBM_EUNSTABLE, "instability: |u|^2 >= c_s^2, rho <= 0 or NaN");
+  if (herr[1]) return fail(c, FSLBM_ETIMEOUT, "a bounded wait for bulk-sweep copies gave up");
   return FSLBM_OK;
 }
 

@@ -10,6 +10,8 @@ namespace fslbm {
 
 template <int Q, class S>
 struct Engine {
+  // the FP32 and 16-bit engines stream the bulk sweep through TMA copies
+  static constexpr bool kTmaBulk = S::kDev && FSLBM_BULK_TMA != 0;
   // persistent bulk blocks per SM the sweep is compiled for
   static constexpr int bulk_blocks_per_sm() {
     return sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2;
@@ -39,19 +41,28 @@ struct Engine {
   static void step(const DPtrs& d, const KParams& p, int parity, int band_grid, int bulk_grid,
                    cudaStream_t st, StageEvents* ev, const Fork* fk) {
     auto bulk = [&](cudaStream_t s2) {
-      if (p.collision == 0)
-        k_bulk<Q, S, 0><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
-      else
-        k_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
+      if constexpr (kTmaBulk) {
+        constexpr size_t sm = tma_smem<Q, typename S::T>();
+        if (p.collision == 0)
+          k_bulk_tma<Q, S, 0><<<bulk_grid, kBulkBlock, sm, s2>>>(d, p, parity);
+        else
+          k_bulk_tma<Q, S, 1><<<bulk_grid, kBulkBlock, sm, s2>>>(d, p, parity);
+      } else {
+        if (p.collision == 0)
+          k_bulk<Q, S, 0><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
+        else
+          k_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
+      }
     };
     const bool forked = fk && !ev;
-    if (ev) ev->mark(0, st);
-    if (forked) {
+    auto fork_bulk = [&]() {
       cudaEventRecord(fk->fork, st);
       cudaStreamWaitEvent(fk->side, fk->fork, 0);
       bulk(fk->side);
       cudaEventRecord(fk->join, fk->side);
-    }
+    };
+    if (ev) ev->mark(0, st);
+    if (forked) fork_bulk();
     k_geometry<Q, S><<<band_grid * kGeoGridMult, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(d, p, parity);
     if (ev) ev->mark(1, st);
     if (!forked) bulk(st);
@@ -116,6 +127,15 @@ struct Engine {
                          (int)geometry_smem<typename S::Real>());
     cudaFuncSetAttribute(kb_geometry<Q, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)geometry_smem<typename S::Real>());
+    if constexpr (kTmaBulk) {
+      cudaFuncSetAttribute(k_bulk_tma<Q, S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tma_smem<Q, typename S::T>());
+      cudaFuncSetAttribute(k_bulk_tma<Q, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tma_smem<Q, typename S::T>());
+      // all persistent blocks resident at once: the most shared memory
+      cudaFuncSetAttribute(k_bulk_tma<Q, S, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(k_bulk_tma<Q, S, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     Ops o;
     o.init_cells = &init_cells;
     o.init_check = &init_check;
@@ -126,9 +146,15 @@ struct Engine {
     o.pdf_out = &pdf_out;
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::Real);
-    o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
-    o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
+    if constexpr (kTmaBulk) {
+      o.bulk_fn[0] = (const void*)&k_bulk_tma<Q, S, 0>;
+      o.bulk_fn[1] = (const void*)&k_bulk_tma<Q, S, 1>;
+    } else {
+      o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
+      o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
+    }
     o.bulk_blocks_per_sm = bulk_blocks_per_sm();
+    o.bulk_smem = kTmaBulk ? tma_smem<Q, typename S::T>() : 0;
     o.batch_step = &batch_step;
     o.batch_bulk_fn[0] = (const void*)&kb_bulk<Q, S, 0>;
     o.batch_bulk_fn[1] = (const void*)&kb_bulk<Q, S, 1>;

@@ -42,6 +42,7 @@ struct Ops {
   const void* bulk_fn[2];  // the bulk sweep kernels (SRT, TRT): graph nodes of
                            // every other kernel get the higher priority
   int bulk_blocks_per_sm;  // resident blocks per SM of the persistent bulk sweep
+  size_t bulk_smem;        // its dynamic shared memory per block
   // one step of every domain of a block table (see DomRec, BatchPlan)
   void (*batch_step)(DomRec* recs, const BatchPlan& plan, int band_grid, int bulk_grid,
                      int collision, cudaStream_t, const Fork*);

@@ -22,7 +22,7 @@
 // plain CPU oracle, so results agree to the last bit.
 #pragma once
 
-#include "fslbm_bulk.cuh"
+#include "fslbm_bulk_tma.cuh"
 
 namespace fslbm {
 
@@ -527,13 +527,16 @@ __global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) k_geometry(DPtrs d, 
 
 // ------------------------------------------------------- interface update
 // Directions whose neighbour data the mass exchange reads ahead at once, and
-// resident blocks of 128 threads per SM the interface kernels are compiled for.
+// resident blocks of 128 threads per SM the FP32/FP16 interface kernels are
+// compiled for (the kernel is latency-bound: four blocks cap it at 128
+// registers a thread; the FP64 engine keeps two).
 #ifndef FSLBM_IFACE_CHUNK
-#define FSLBM_IFACE_CHUNK 9
+#define FSLBM_IFACE_CHUNK 1
 #endif
 #ifndef FSLBM_IFACE_MINB
 #define FSLBM_IFACE_MINB 1
 #endif
+
 constexpr int kIfaceChunk = FSLBM_IFACE_CHUNK;
 constexpr int kIfaceMinBlocks = FSLBM_IFACE_MINB;
 // Pull with the free-surface BC (Eq. nm-fslbm-boundary-condition) on the
@@ -671,8 +674,8 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     // (new interface cells average them over their neighbours)
     R mu[3];
     if constexpr (S::kDev) {
-      // the density as the stored PDFs hold it (FP64 sum of stored values):
-      // the mass a conversion to liquid hands over to the PDFs
+      // the density as the stored PDFs hold it (FP64 sum of the stored
+      // values): the mass a conversion to liquid hands over to them
       double sd = 0.0;
       R fs[Q];
 #pragma unroll
@@ -718,7 +721,7 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
   }
 
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128, kIfaceMinBlocks) k_interface(DPtrs d, KParams p, int parity) {
+__global__ void __launch_bounds__(128, (sizeof(typename S::Real) == 4 ? kIfaceMinBlocks : 2)) k_interface(DPtrs d, KParams p, int parity) {
   const int n = d.counts[parity];
   bool bad = false;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
@@ -900,8 +903,11 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
       return;
     }
     const double m0 = d.mass[c];
+    // an interface cell that no converted cell flagged receives nothing:
+    // m + 0 and (m + 0) / rho are the m and phi that k_resolve stored
+    // (m_next and phi_next = m_next / rho), unless m is -0
+    if (!gather && !(m0 == 0.0 && signbit(m0))) return;
     const double rb = d.rho_band[k];
-    // an interface cell that no converted cell flagged receives nothing
     double s = 0.0;
     if (gather) {
       decode(p, c, x, y, z);
@@ -1323,7 +1329,7 @@ __global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? k
 }
 
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128, kIfaceMinBlocks) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
+__global__ void __launch_bounds__(128, (sizeof(typename S::Real) == 4 ? kIfaceMinBlocks : 2)) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
   const int total = pl.band[pl.n];
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     const int k = find_domain(pl.band, pl.n, g);
