@@ -335,8 +335,8 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   if (!c) return FSLBM_EINVAL;
   if (!fill || !flags) return fail(c, FSLBM_EINVAL, "fill and flags are required");
   const size_t N = (size_t)c->kp.N;
-  for (size_t i = 0; i < N; ++i)
-    if (flags[i] > 3) return fail(c, FSLBM_EINVAL, "flag value > 3");
+  // flag values and the closed interface layer are checked on the device
+  // (k_init_check) once the flags are uploaded
   cudaStream_t st = c->stream;
   uint8_t* raw = nullptr;
   double *dfill = nullptr, *dvel = nullptr, *dden = nullptr;
@@ -374,8 +374,8 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   if (hbad) {
     cleanup();
     return fail(c, FSLBM_EINVAL,
-                (hbad & 2) ? "a liquid cell touches a gas cell (interface layer not closed)"
-                           : "flag value > 3");
+                (hbad & 1) ? "flag value > 3"
+                           : "a liquid cell touches a gas cell (interface layer not closed)");
   }
   // bubbles: connected gas regions labelled on the device, fixed-point
   // initial volumes
