@@ -880,12 +880,15 @@ template <int Q, class S>
 __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int parity, int k) {
   using R = typename S::Real;
   using T = typename S::T;
-  const int nb_ = d.counts[parity];
+  // the new cells come first: their dependent chains are the longest, so
+  // they start with the launch
+  const int nnew = d.counts[2];
   T* __restrict__ B = (T*)d.pdf[parity ^ 1];
   const long long Np = p.Np;
 
-  const bool is_band = k < nb_;
-  const int c = is_band ? d.band[parity][k] : d.newlist[k - nb_];
+  const bool is_band = k >= nnew;
+  if (is_band) k -= nnew;
+  const int c = is_band ? d.band[parity][k] : d.newlist[k];
   int x, y, z;
   int nid[Q];
   if (is_band) {
@@ -959,12 +962,37 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
     }
     double sr = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
     int cnt = 0;
-    // moments cached by the interface kernel, read a few directions at a
-    // time; liquid neighbours (none next to a gas cell while the interface
-    // layer is closed) form theirs from the stored PDFs
+    unsigned liq_use = 0u;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (((use >> i) & 1u) && field2(ntm, i) == T_LIQ) liq_use |= 1u << i;
+    if (liq_use) {
+      // liquid neighbours (none next to a gas cell while the interface layer
+      // is closed) form their moments from the stored PDFs: direction order
+      for (int i = 1; i < Q; ++i) {
+        if (!((use >> i) & 1u)) continue;
+        double rn;
+        R un[3];
+        if (field2(ntm, i) == T_IFACE) {
+          const R* mu = (const R*)d.mom_u;
+          rn = d.mom_rho[nid[i]];
+          un[0] = mu[3LL * nid[i] + 0];
+          un[1] = mu[3LL * nid[i] + 1];
+          un[2] = mu[3LL * nid[i] + 2];
+        } else {
+          post_moments<Q, S>(B, Np, nid[i], p, rn, un);
+        }
+        sr = sr + rn;
+        sx = sx + (double)un[0];
+        sy = sy + (double)un[1];
+        sz = sz + (double)un[2];
+        ++cnt;
+      }
+    }
+    // moments cached by the interface kernel, read a few directions at a time
     constexpr int kChunk = 5;
 #pragma unroll
-    for (int i0 = 1; i0 < Q; i0 += kChunk) {
+    for (int i0 = 1; liq_use == 0u && i0 < Q; i0 += kChunk) {
       double rn[kChunk];
       R un[kChunk][3];
 #pragma unroll
@@ -982,7 +1010,6 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
       for (int a = 0; a < kChunk; ++a) {
         const int i = i0 + a;
         if (i >= Q || !((use >> i) & 1u)) continue;
-        if (field2(ntm, i) != T_IFACE) post_moments<Q, S>(B, Np, nid[i], p, rn[a], un[a]);
         sr = sr + rn[a];
         sx = sx + (double)un[a][0];
         sy = sy + (double)un[a][1];
