@@ -90,14 +90,37 @@ __device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int 
   }
 }
 
+// Warp-sized units of the list are handed out kBulkChunk consecutive ones at
+// a time from a per-step counter (counts[6]: zero at init, cleared again by
+// the finalize kernel of every step), so a warp sweeps neighbouring
+// segments one after another while the 32-byte sectors they share are still
+// in L2, and the grid works on one front of the list.  0 = a fixed stride
+// over the list.
+#ifndef FSLBM_BULK_DYN
+#define FSLBM_BULK_DYN 4
+#endif
+constexpr int kBulkChunk = FSLBM_BULK_DYN;
+
 template <int Q, class S, int COLL>
 __global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
     k_bulk(DPtrs d, KParams p, int parity) {
   constexpr int kGroups = 32 / kSegCells;
   const int nseg = d.counts[5];
-  const int warps = (gridDim.x * kBulkBlock) >> 5;
-  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
-    bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
+  if constexpr (kBulkChunk > 0) {
+    const int nw = (nseg + kGroups - 1) / kGroups;
+    for (;;) {
+      int base = 0;
+      if ((threadIdx.x & 31) == 0) base = atomicAdd(&d.counts[6], kBulkChunk);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= nw) break;
+      const int end = base + kBulkChunk < nw ? base + kBulkChunk : nw;
+      for (int w = base; w < end; ++w) bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
+    }
+  } else {
+    const int warps = (gridDim.x * kBulkBlock) >> 5;
+    for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
+      bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
+  }
 }
 
 }  // namespace fslbm

@@ -1196,6 +1196,7 @@ __device__ __forceinline__ void finalize_warp(const DPtrs& d, const KParams& p, 
 
 static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, int parity) {
   const int total = d.counts[parity] + d.counts[2];
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.counts[6] = 0;  // the next step's bulk hand-out
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int base = wid * 32; base < total; base += warps * 32) finalize_warp(d, p, parity, base);
