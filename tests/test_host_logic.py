@@ -77,3 +77,19 @@ def test_batch_and_request_seeds_are_reproducible():
     r2 = S.drop_requests(n=10)
     assert [t for t, _ in r1] == [t for t, _ in r2]
     assert all(96 <= kw["L"] <= 256 and 0.08 <= kw["R_frac"] <= 0.15 for _, kw in r1)
+
+
+def test_sector_census_bounds():
+    """The bulk sweep's sector census (bench.py --sector-census) on the dam
+    break: every count lies between the algorithmic bytes and the whole-line
+    bound, in the order the memory hierarchy implies."""
+    import bench
+    c = bench.sector_census("dam_break")
+    assert c["liquid_cells"] > 0 and 0.0 < c["lane_occupancy"] <= 1.0
+    assert c["segments"] >= c["liquid_cells"] / 32
+    distinct = c["distinct_read_sectors"]
+    # 19 FP32 pulls per liquid cell can never fit in fewer sectors than bytes / 32
+    assert distinct * 32 >= c["algorithmic_read_MB"] * 1e6 - 1
+    assert distinct <= c["warp_sector_requests"]
+    assert distinct <= c["read_sectors_64B_chunks"] <= c["read_sectors_128B_lines"]
+    assert c["partial_write_sectors"] >= 0 and c["reflected_write_sectors"] >= 0
