@@ -134,7 +134,8 @@ fslbm_status fslbm_batch_create(fslbm_ctx* const* members, int n, void* stream, 
   b->tune.band_blocks_per_sm = 2;
   b->tune.ms_per_step = 0.0;
   cudaError_t e = cudaMalloc(&b->d_recs, (size_t)n * sizeof(DomRec));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_off, 4 * (size_t)(n + 1) * sizeof(int));
+  // four prefix arrays of n + 1 entries, then the bulk sweep's hand-out counter
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_off, (4 * (size_t)(n + 1) + 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->fork.side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.fork, cudaEventDisableTiming);

@@ -1319,6 +1319,7 @@ __device__ __forceinline__ int round32(int v) { return (v + 31) & ~31; }
 // fills and lays out tiles, bulk warp units and band cells.
 static __global__ void kb_plan_front(DomRec* recs, BatchPlan pl) {
   constexpr int kGroups = 32 / kSegCells;
+  if (threadIdx.x == 0) *(pl.all + pl.n + 1) = 0;  // kb_bulk's hand-out counter
   for (int k = threadIdx.x; k < pl.n; k += blockDim.x) reset_step_counts(recs[k].d, recs[k].parity);
   __syncthreads();
   block_prefix(pl.n, pl.tiles, [&](int k) { return recs[k].d.counts[3 + recs[k].parity]; });
@@ -1344,15 +1345,32 @@ __global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) kb_geometry(const Do
   }
 }
 
+// The batch's bulk hand-out counter: the int after the four prefix arrays
+// of the plan (n + 1 entries each), cleared by kb_plan_front every step.
+__device__ __forceinline__ int* batch_bulk_ctr(const BatchPlan& pl) { return pl.all + pl.n + 1; }
+
+// Units of all domains handed out as in k_bulk, kBulkChunk at a time.
 template <int Q, class S, int COLL>
 __global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
     kb_bulk(const DomRec* __restrict__ recs, BatchPlan pl) {
   const int total = pl.bulk[pl.n];
-  const int warps = (gridDim.x * kBulkBlock) >> 5;
-  for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w < total; w += warps) {
+  auto unit = [&](int w) {
     const int k = find_domain(pl.bulk, pl.n, w);
     const DomRec& r = recs[k];
     bulk_unit<Q, S, COLL>(r.d, r.p, r.parity, w - pl.bulk[k], r.d.counts[5]);
+  };
+  if constexpr (kBulkChunk > 0) {
+    for (;;) {
+      int base = 0;
+      if ((threadIdx.x & 31) == 0) base = atomicAdd(batch_bulk_ctr(pl), kBulkChunk);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= total) break;
+      const int end = base + kBulkChunk < total ? base + kBulkChunk : total;
+      for (int w = base; w < end; ++w) unit(w);
+    }
+  } else {
+    const int warps = (gridDim.x * kBulkBlock) >> 5;
+    for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w < total; w += warps) unit(w);
   }
 }
 
