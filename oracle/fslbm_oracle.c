@@ -970,18 +970,33 @@ int orc_bubbles(const orc* o, double* volume, double* pressure, int* ids_cell,
   return o->nb;
 }
 
+/* Total mass: the density of every liquid cell plus the mass of every
+ * interface cell.  The cells' contributions are summed with Neumaier's
+ * compensated summation, so the result carries no accumulation error that
+ * grows with the number of cells (the mass balance is judged at 1e-12). */
 double orc_total_mass(const orc* o) {
   long c;
   int i;
-  double M = 0.0;
+  double M = 0.0, comp = 0.0;
   for (c = 0; c < o->N; ++c) {
+    double x;
     if (o->flag[c] == LIQ) {
       double r = 0.0;
       for (i = 0; i < o->L.q; ++i) r = r + o->f[i * o->N + c];
-      M = M + r;
+      x = r;
     } else if (o->flag[c] == IFACE) {
-      M = M + o->m[c];
+      x = o->m[c];
+    } else {
+      continue;
+    }
+    {
+      const double t = M + x;
+      if (fabs(M) >= fabs(x))
+        comp += (M - t) + x;
+      else
+        comp += (x - t) + M;
+      M = t;
     }
   }
-  return M;
+  return M + comp;
 }

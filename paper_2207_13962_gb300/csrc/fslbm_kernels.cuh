@@ -1225,7 +1225,9 @@ __global__ void __launch_bounds__(kBlock) k_obs_partial(DPtrs d, KParams p, int 
                                                         double* part) {
   using R = typename S::Real;
   const typename S::T* P = (const typename S::T*)d.pdf[parity];
-  double mass = 0.0, umax = 0.0, vol = 0.0, nan = 0.0, cnt[4] = {0, 0, 0, 0};
+  // the mass is summed per thread with Neumaier's compensation, then
+  // pairwise across threads and blocks
+  double mass = 0.0, mcomp = 0.0, umax = 0.0, vol = 0.0, nan = 0.0, cnt[4] = {0, 0, 0, 0};
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < p.N; c += gridDim.x * blockDim.x) {
     const int t = d.flags[c] & F_TYPE;
     cnt[t] += 1.0;
@@ -1236,13 +1238,18 @@ __global__ void __launch_bounds__(kBlock) k_obs_partial(DPtrs d, KParams p, int 
       const double uu = sqrt((double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
       if (!(uu == uu) || !(r > 0.0)) nan = 1.0;
       if (uu > umax) umax = uu;
-      mass += (t == T_LIQ) ? r : d.mass[c];
+      {
+        const double x = (t == T_LIQ) ? r : d.mass[c];
+        const double s = mass + x;
+        mcomp += (fabs(mass) >= fabs(x)) ? ((mass - s) + x) : ((x - s) + mass);
+        mass = s;
+      }
       vol += d.phi[c];
       if (!(d.mass[c] == d.mass[c])) nan = 1.0;
     }
   }
   __shared__ double sh[kObsFields][kBlock / 32];
-  double v[kObsFields] = {mass, umax, vol, nan, cnt[0], cnt[1], cnt[2], cnt[3]};
+  double v[kObsFields] = {mass + mcomp, umax, vol, nan, cnt[0], cnt[1], cnt[2], cnt[3]};
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int f = 0; f < kObsFields; ++f) {
