@@ -868,10 +868,12 @@ static void convert(orc* o) {
       o->bid[c] = best;
     }
   }
-  /* excess mass: receivers gather shares in direction order (R15) */
+  /* excess mass: receivers gather shares in direction order (R15).  The
+   * receivers are the cells counted above; a deferred cell was not counted
+   * (its flag was not interface then), so it keeps its mass. */
   for (c = 0; c < N; ++c) {
     double s = 0.0;
-    if (o->nflag[c] != IFACE) continue;
+    if (o->nflag[c] != IFACE || o->dfr[c]) continue;
     coords(o, c, &x, &y, &z);
     for (i = 1; i < q; ++i) {
       long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);

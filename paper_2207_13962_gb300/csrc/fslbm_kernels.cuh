@@ -905,6 +905,9 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
       d.mass[c] = 0.0;
       return;
     }
+    // a deferred cell stays interface and keeps its mass: it was not counted
+    // among its converting neighbours' receivers
+    if (f == CV_DEFER) return;
     const double m0 = d.mass[c];
     // an interface cell that no converted cell flagged receives nothing:
     // m + 0 and (m + 0) / rho are the m and phi that k_resolve stored

@@ -202,3 +202,91 @@ def test_bubble_labels_are_connected_components():
         expect = cells.sum() + np.sum(1.0 - fill.reshape(-1)[iface])
         assert abs(V[b] - expect) < 1e-6
     assert np.all(ids[~gas & (flags.reshape(-1) == S.LIQ)] == -1)
+
+
+# ---------------------------------------------------------------- conversion
+# Tiny all-interface domains at rest (f = w_i, no force, periodic): every
+# cell is of standard class and every exchange term is a - b = 0, so one
+# step changes masses only through conversion and excess redistribution.
+
+def _conversion_step(fill):
+    n = fill.shape[0]
+    o = Oracle(n, n, n, periodic=(True, True, True), variant="OM")
+    o.init(fill.reshape(-1), np.full(n ** 3, S.IFACE, np.uint8), None, None)
+    m0 = fill.copy()  # rho = 1 at rest: m = phi
+    M0 = o.total_mass()
+    o.step(1)
+    r = o.read()
+    return (r["flags"].reshape(fill.shape), r["mass"].reshape(fill.shape), M0, o.total_mass(), m0)
+
+
+def _d3q19_neighbours(c, n):
+    out = []
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if (dx, dy, dz) != (0, 0, 0) and abs(dx) + abs(dy) + abs(dz) <= 2:
+                    out.append(((c[0] + dz) % n, (c[1] + dy) % n, (c[2] + dx) % n))
+    return out
+
+
+def test_excess_of_one_converting_cell_is_split_evenly():
+    # Eq. nm-fslbm-excess-mass: m - rho goes in equal shares to the interface
+    # cells around it after conversion (here all 18 lattice neighbours)
+    n = 7
+    fill = np.full((n, n, n), 0.5)
+    fill[3, 3, 3] = 1.05
+    flags, mass, M0, M1, m0 = _conversion_step(fill)
+    assert flags[3, 3, 3] == S.LIQ
+    assert np.count_nonzero(flags == S.LIQ) == 1 and np.count_nonzero(flags == S.GAS) == 0
+    gain = mass - m0
+    nb = _d3q19_neighbours((3, 3, 3), n)
+    share = gain[nb[0]]
+    assert share > 0
+    for c in nb:
+        assert abs(gain[c] - share) < 1e-15
+    assert abs(18 * share - 0.05) < 1e-14
+    others = np.ones(fill.shape, bool)
+    others[3, 3, 3] = False
+    for c in nb:
+        others[c] = False
+    assert np.abs(gain[others]).max() == 0.0
+    assert abs(M1 - M0) < 1e-13 * M0
+
+
+def test_conflict_rule_keeps_the_emptying_neighbour_interface():
+    # R13: a cell marked for gas next to a cell marked for liquid stays
+    # interface; it is then a receiver of the converting cell's excess
+    n = 7
+    fill = np.full((n, n, n), 0.5)
+    fill[3, 3, 3] = 1.05
+    fill[3, 3, 4] = -0.05
+    flags, mass, M0, M1, m0 = _conversion_step(fill)
+    assert flags[3, 3, 3] == S.LIQ and flags[3, 3, 4] == S.IFACE
+    assert np.count_nonzero(flags == S.GAS) == 0
+    assert abs(mass[3, 3, 4] - (-0.05 + 0.05 / 18)) < 1e-14
+    assert abs(M1 - M0) < 1e-13 * M0
+    # apart, both convert: the emptying cell hands its (negative) mass on
+    fill[3, 3, 4] = 0.5
+    fill[3, 3, 0] = -0.05
+    flags, mass, M0, M1, m0 = _conversion_step(fill)
+    assert flags[3, 3, 3] == S.LIQ and flags[3, 3, 0] == S.GAS
+    assert abs(M1 - M0) < 1e-13 * M0
+
+
+def test_deferred_cell_keeps_its_mass():
+    # R15: the centre of a 3x3x3 block of overfull cells has only converting
+    # neighbours, hence no receiver: its conversion is deferred, it stays
+    # interface with its mass, and takes no share of its neighbours' excess
+    # (they did not count it as a receiver) -- mass is conserved
+    n = 9
+    fill = np.full((n, n, n), 0.5)
+    fill[3:6, 3:6, 3:6] = 1.05
+    flags, mass, M0, M1, m0 = _conversion_step(fill)
+    assert flags[4, 4, 4] == S.IFACE
+    block = np.zeros(fill.shape, bool)
+    block[3:6, 3:6, 3:6] = True
+    block[4, 4, 4] = False
+    assert np.all(flags[block] == S.LIQ)
+    assert abs(mass[4, 4, 4] - 1.05) < 1e-14
+    assert abs(M1 - M0) < 1e-13 * M0
