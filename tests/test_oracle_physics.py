@@ -290,3 +290,46 @@ def test_deferred_cell_keeps_its_mass():
     assert np.all(flags[block] == S.LIQ)
     assert abs(mass[4, 4, 4] - 1.05) < 1e-14
     assert abs(M1 - M0) < 1e-13 * M0
+
+
+def test_new_interface_cells_from_gas_and_liquid():
+    # R14 and the claim rule.  A gas cell next to a cell that fills becomes
+    # interface with f = f^eq(mean rho, mean u) of its fluid neighbours; at
+    # rest (and with rho^G = 3 p^V = 1, sigma = 0, so the free-surface BC
+    # reconstructs w_i) that is w_i.  A liquid cell next to a cell that
+    # empties becomes interface.  Cells next to gas are of class NF (and next
+    # to liquid of class NE), so they exchange mass with their standard
+    # neighbours even at rest (R12); the fills are chosen far enough past
+    # the thresholds that the conversions happen all the same.
+    n = 7
+    _, w, _ = lattice(19)
+
+    def run(flags, fill):
+        o = Oracle(n, n, n, periodic=(True, True, True), variant="OM")
+        o.init(fill.reshape(-1), flags.reshape(-1), None, None)
+        M0 = o.total_mass()
+        o.step(1)
+        r = o.read()
+        assert abs(o.total_mass() - M0) < 1e-13 * M0
+        assert _closed(r["flags"], (n, n, n), (True, True, True), 19)
+        return r, r["flags"].reshape(n, n, n)
+
+    fill = np.full((n, n, n), 0.5)
+    flags = np.full((n, n, n), S.IFACE, np.uint8)
+    flags[3, 3, 4], fill[3, 3, 4] = S.GAS, 0.0
+    fill[3, 3, 3] = 2.5  # fills, next to the gas cell
+    r, fl = run(flags, fill)
+    assert fl[3, 3, 3] == S.LIQ and fl[3, 3, 4] == S.IFACE
+    g = np.ravel_multi_index((3, 3, 4), (n, n, n))
+    np.testing.assert_allclose(r["pdf"][:, g], w, rtol=0, atol=1e-15)
+    assert r["mass"][g] > 0.0  # 0 plus its share of the filled cell's excess
+
+    fill = np.full((n, n, n), 0.5)
+    flags = np.full((n, n, n), S.IFACE, np.uint8)
+    flags[3, 3, 4], fill[3, 3, 4] = S.LIQ, 1.0
+    fill[3, 3, 3] = -1.5  # empties, next to the liquid cell
+    r, fl = run(flags, fill)
+    assert fl[3, 3, 3] == S.GAS and fl[3, 3, 4] == S.IFACE
+    l = np.ravel_multi_index((3, 3, 4), (n, n, n))
+    # m = rho of its PDFs, then its (negative) share of the emptied cell's mass
+    assert r["mass"][l] < r["pdf"][:, l].sum()
