@@ -333,3 +333,25 @@ def test_new_interface_cells_from_gas_and_liquid():
     l = np.ravel_multi_index((3, 3, 4), (n, n, n))
     # m = rho of its PDFs, then its (negative) share of the emptied cell's mass
     assert r["mass"][l] < r["pdf"][:, l].sum()
+
+
+def test_thuerey_classes_exchange_antisymmetrically():
+    # R12: two interface layers between gas and liquid, so the interface
+    # pairs are NF (gas side) against NE (liquid side).  Every entry of the
+    # class table must be antisymmetric for the total mass to stay exact.
+    nx, ny, nz = 10, 4, 4
+    flags = np.full((nz, ny, nx), S.LIQ, np.uint8)
+    fill = np.ones((nz, ny, nx))
+    flags[:, :, :3] = S.GAS
+    fill[:, :, :3] = 0.0
+    flags[:, :, 3:5] = S.IFACE
+    fill[:, :, 3] = 0.3
+    fill[:, :, 4] = 0.8
+    rng = np.random.default_rng(11)
+    fill[:, :, 3:5] += rng.uniform(-0.05, 0.05, (nz, ny, 2))
+    o = Oracle(nx, ny, nz, periodic=(False, True, True), variant="OM", sigma=1e-3)
+    o.init(fill.reshape(-1), flags.reshape(-1), None, None)
+    M0 = o.total_mass()
+    o.step(20)
+    assert abs(o.total_mass() - M0) < 1e-13 * M0
+    assert _closed(o.read()["flags"], (nx, ny, nz), (False, True, True), 19)
