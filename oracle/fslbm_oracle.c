@@ -49,7 +49,9 @@
  *       neighbours that are liquid or old interface after conversion.
  *   R15 excess mass m_ex = m - rho (to liquid) or m (to gas), split evenly over
  *       neighbours that are interface after conversion; no receiver -> the
- *       conversion is deferred.  Receivers sum shares in direction order.
+ *       conversion is deferred, and the cell stays interface with its mass
+ *       (it was not counted as a receiver, so it takes no share).  Receivers
+ *       sum shares in direction order.
  *   R16 K8 kernel (1 - r^2/4)^4 on the 3x3x3 block (zero at r >= 2), weights
  *       normalised by their sum; obstacle / out-of-domain -> centre value.
  *   R17 Parker-Youngs weights 4 (face centre), 2 (edge), 1 (corner); obstacle
