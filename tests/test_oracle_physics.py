@@ -355,3 +355,26 @@ def test_thuerey_classes_exchange_antisymmetrically():
     o.step(20)
     assert abs(o.total_mass() - M0) < 1e-13 * M0
     assert _closed(o.read()["flags"], (nx, ny, nz), (False, True, True), 19)
+
+
+def test_bubble_volume_and_pressure_follow_the_fields():
+    # Eq. nm-fslbm-pressure-volume: after the bubble has moved and its
+    # surface cells converted, V_b still equals #gas + sum over its interface
+    # cells of (1 - phi) recounted from the fields (to the 2^-32 fixed-point
+    # resolution per cell), and p^V_b V_b = p^V(0) V_b(0)
+    sc = S.taylor_bubble(nx=24, ny=24, nz=60, D=20, bubble_d=12, bubble_len=16, z0=10, z_ref=30.0,
+                         g=2e-4, sigma=1e-3)
+    o = _run(sc)
+    V0, P0, _ = o.bubbles()
+    o.step(40)
+    V, P, ids = o.bubbles()
+    r = o.read()
+    fl, fill = r["flags"], r["fill"]
+    assert len(V) == len(V0) == 1
+    gas = (fl == S.GAS) & (ids == 0)
+    iface = (fl == S.IFACE) & (ids == 0)
+    assert iface.sum() > 0
+    expect = gas.sum() + np.sum(1.0 - fill[iface])
+    assert abs(V[0] - expect) <= (iface.sum() + 1) * 2.0 ** -32
+    assert V[0] != V0[0]  # the bubble did change
+    assert abs(P[0] * V[0] - P0[0] * V0[0]) <= 1e-14 * P0[0] * V0[0]
