@@ -49,7 +49,8 @@ typedef enum {
                            (the instability of Sec. 4.2); fields stay readable */
   FSLBM_ETIMEOUT = 5,   /* a bounded device wait gave up                     */
   FSLBM_ESTATE = 6,     /* call out of order (e.g. step before init)         */
-  FSLBM_ECAPACITY = 7   /* the interface band outgrew its preallocated list  */
+  FSLBM_ECAPACITY = 7   /* a list outgrew its capacity (not returned: the
+                           interface and new-cell lists hold every cell) */
 } fslbm_status;
 
 /* Velocity sets D3Q19 and D3Q27 (Sec. 2.1). */
@@ -141,7 +142,8 @@ fslbm_status fslbm_init(fslbm_ctx* ctx, const double* fill, const uint8_t* flags
 fslbm_status fslbm_step(fslbm_ctx* ctx, int n);
 
 /* Wait for the stream; FSLBM_EUNSTABLE if an instability was flagged,
- * FSLBM_ECAPACITY if the interface band overflowed. */
+ * FSLBM_ETIMEOUT if a bounded device wait gave up (only the TMA-staged bulk
+ * sweep waits on the device; it is not built by default). */
 fslbm_status fslbm_sync(fslbm_ctx* ctx);
 
 /* Whole-domain observables; synchronizes.  Returns FSLBM_EUNSTABLE (with
