@@ -15,7 +15,7 @@ def _declared():
     return sorted(set(re.findall(r"\b(fslbm_[a-z_0-9]+)\s*\(", src)))
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_step_calls():
     names = _declared()
     for n in ("fslbm_create", "fslbm_init", "fslbm_step", "fslbm_observables", "fslbm_destroy"):
         assert n in names
