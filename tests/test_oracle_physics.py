@@ -19,6 +19,7 @@ import pytest
 from scipy.optimize import curve_fit
 
 from oracle import Oracle, lattice
+from oracle.oracle import feq as orc_feq
 from paper_2207_13962_gb300 import scenarios as S
 
 VARIANTS = ["NBRC", "NBKC", "OM", "OM3"]
@@ -378,3 +379,36 @@ def test_bubble_volume_and_pressure_follow_the_fields():
     assert abs(V[0] - expect) <= (iface.sum() + 1) * 2.0 ** -32
     assert V[0] != V0[0]  # the bubble did change
     assert abs(P[0] * V[0] - P0[0] * V0[0]) <= 1e-14 * P0[0] * V0[0]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_slab_in_uniform_tangential_motion_is_steady(variant):
+    # R8: the free-surface BC takes the interface cell's own velocity.  A
+    # liquid slab moving uniformly along its two flat surfaces (periodic, no
+    # force, p^G = p^V = 1/3 so rho^G = 1) is an exact steady state: every
+    # reconstructed PDF equals f^eq(1, U), the mass exchange along the
+    # surface cancels, and nothing changes.  A BC velocity other than U
+    # leaves an O(U^2) error in the reconstructed PDFs that builds up.
+    nx, ny, nz = 8, 12, 4
+    U = np.array([0.05, 0.0, 0.03])
+    fl = np.full((nz, ny, nx), S.GAS, np.uint8)
+    fill = np.zeros((nz, ny, nx))
+    fl[:, 4:8, :] = S.LIQ
+    fill[:, 4:8, :] = 1.0
+    for y in (3, 8):
+        fl[:, y, :] = S.IFACE
+        fill[:, y, :] = 0.5
+    fluid = (fl == S.LIQ) | (fl == S.IFACE)
+    N = nx * ny * nz
+    vel = np.zeros(3 * N)
+    for a in range(3):
+        vel[a * N:(a + 1) * N] = np.where(fluid.reshape(-1), U[a], 0.0)
+    o = Oracle(nx, ny, nz, periodic=(True, True, True), variant=variant)
+    o.init(fill.reshape(-1), fl.reshape(-1), vel, None)
+    feq = orc_feq(19, 1.0, U)
+    o.step(50)
+    r = o.read()
+    np.testing.assert_array_equal(r["flags"], fl.reshape(-1))
+    np.testing.assert_allclose(r["fill"][fluid.reshape(-1)], fill.reshape(-1)[fluid.reshape(-1)], rtol=0, atol=1e-12)
+    f = r["pdf"][:, fluid.reshape(-1)]
+    np.testing.assert_allclose(f, np.repeat(feq[:, None], f.shape[1], 1), rtol=0, atol=1e-12)
