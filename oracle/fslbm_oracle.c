@@ -27,8 +27,12 @@
  *   R3  n = grad(phi~) points into the liquid; NBRC/NBKC use n.c_i >= 0 / > 0.
  *   R4  NBRC/NBKC also reconstruct every missing PDF (i in G-) outside the
  *       normal-based set.
- *   R5  ties n.c_i = 0 (i != 0) are evaluated exactly on the normalised normal:
- *       NBRC reconstructs them, NBKC only if missing.
+ *   R5  ties: a direction with |n^.c_i| <= 2^-20 on the normalised normal
+ *       counts as n.c_i = 0 (Appendix A assumes that only c_0 ties; at mirror
+ *       planes of the interface a component of n^ is zero in exact
+ *       arithmetic and rounding-sized otherwise, so an exact sign test would
+ *       decide by rounding noise).  NBRC reconstructs ties, NBKC only missing
+ *       ones.
  *   R6  OM3 falls back to NBKC (selectable NBRC) when |G-| < 3.
  *   R7  gas density rho^G = 3 (p^V + sigma kappa), kappa = -div(n^) with n^
  *       pointing into the liquid (sum of principal curvatures).
@@ -62,6 +66,10 @@
  *       of their gas neighbours; volume V = #gas + sum over interface (1-phi)
  *       accumulated in fixed point with 2^-32 resolution.
  *   R20 cells outside a non-periodic boundary act as no-slip obstacle cells.
+ *
+ * R8 has one exception: a gas cell that becomes interface gets f^eq of the
+ * mean density and velocity of its neighbours (R14), with no collision, so
+ * R8 evaluates its velocity as that mean minus g/2 until its first collision.
  */
 #include "fslbm_oracle.h"
 
@@ -274,8 +282,12 @@ static double ndot(const lattice* L, int i, const double* n) {
          (double)L->c[i][2] * n[2];
 }
 
+/* Width of the tie band of reading R5: |n^.c_i| <= TIE counts as a tie. */
+#define TIE 0x1p-20
+
 /* Sets R of Sec. 3 (Eqs. fsbcv-nbrc, fsbcv-nbkc, fsbcv-om-sets, fsbcv-om3)
- * with readings R3-R6. */
+ * with readings R3-R6: NBRC takes n.c_i >= 0 (ties included), NBKC
+ * n.c_i > 0 (ties excluded), both with every missing PDF. */
 static void select_R(const lattice* L, int variant, int om3_fallback,
                      const double* nhat, const int* miss, int* recon) {
   int i, nmiss = 0, v = variant;
@@ -283,8 +295,9 @@ static void select_R(const lattice* L, int variant, int om3_fallback,
   if (v == 4) v = (nmiss >= 3) ? 3 : om3_fallback;
   for (i = 0; i < L->q; ++i) {
     int r = miss[i] ? 1 : 0;
-    if (v == 1 && ndot(L, i, nhat) >= 0.0) r = 1;
-    if (v == 2 && ndot(L, i, nhat) > 0.0) r = 1;
+    double d = ndot(L, i, nhat);
+    if (v == 1 && d >= -TIE) r = 1;
+    if (v == 2 && d > TIE) r = 1;
     recon[i] = r;
   }
 }
@@ -566,26 +579,73 @@ static double k8(int dx, int dy, int dz) {
   return t * t * t * t;
 }
 
-static void geometry(orc* o) {
-  long N = o->N, c;
-  int x, y, z, dx, dy, dz;
-  double wsum = 0.0;
+/* Blocks of 3x3x3 values around a cell, b[(dx+1) + 3 (dy+1) + 9 (dz+1)]. */
+#define BLK(dx, dy, dz) ((dx) + 1 + 3 * ((dy) + 1) + 9 * ((dz) + 1))
+
+/* Smoothed fill level at the centre of a block of fill levels (R16):
+ * sum K8(r) phi / sum K8(r), summed over dz, dy, dx in that order. */
+static double k8_smooth(const double* b) {
+  double s = 0.0, wsum = 0.0;
+  int dx, dy, dz;
   for (dz = -1; dz <= 1; ++dz)
     for (dy = -1; dy <= 1; ++dy)
       for (dx = -1; dx <= 1; ++dx) wsum = wsum + k8(dx, dy, dz);
-  /* smoothed fill level on every non-obstacle cell */
-  for (c = 0; c < N; ++c) {
+  for (dz = -1; dz <= 1; ++dz)
+    for (dy = -1; dy <= 1; ++dy)
+      for (dx = -1; dx <= 1; ++dx) s = s + k8(dx, dy, dz) * b[BLK(dx, dy, dz)];
+  return s / wsum;
+}
+
+/* Parker-Youngs gradient at the centre of a block of smoothed fill levels
+ * (Eq. nm-fslbm-normal, R17): for axis a, the differences across the two
+ * faces normal to a, weighted 4 (face centre), 2 (edge), 1 (corner); p runs
+ * over the slower, r over the faster of the two other axes. */
+static void py_gradient(const double* b, double* n3) {
+  int a;
+  for (a = 0; a < 3; ++a) {
     double s = 0.0;
+    int p, r;
+    for (p = -1; p <= 1; ++p)
+      for (r = -1; r <= 1; ++r) {
+        int d1[3], d2[3];
+        double w;
+        if (a == 0) {
+          d1[0] = 1; d1[1] = r; d1[2] = p;
+        } else if (a == 1) {
+          d1[0] = r; d1[1] = 1; d1[2] = p;
+        } else {
+          d1[0] = r; d1[1] = p; d1[2] = 1;
+        }
+        d2[0] = d1[0];
+        d2[1] = d1[1];
+        d2[2] = d1[2];
+        d2[a] = -1;
+        w = (p == 0 && r == 0) ? 4.0 : (p == 0 || r == 0) ? 2.0 : 1.0;
+        s = s + w * (b[BLK(d1[0], d1[1], d1[2])] - b[BLK(d2[0], d2[1], d2[2])]);
+      }
+    n3[a] = s;
+  }
+}
+
+double orc_k8_smooth(const double* block27) { return k8_smooth(block27); }
+void orc_py_gradient(const double* block27, double* n3) { py_gradient(block27, n3); }
+
+static void geometry(orc* o) {
+  long N = o->N, c;
+  int x, y, z, dx, dy, dz;
+  double b[27];
+  /* smoothed fill level on every non-obstacle cell; obstacle and
+   * out-of-domain stencil points take the centre's value */
+  for (c = 0; c < N; ++c) {
     if (o->flag[c] == OBST) continue;
     coords(o, c, &x, &y, &z);
     for (dz = -1; dz <= 1; ++dz)
       for (dy = -1; dy <= 1; ++dy)
         for (dx = -1; dx <= 1; ++dx) {
           long n = nbr(o, x, y, z, dx, dy, dz);
-          double v = (nflag_of(o, n) == OBST) ? o->phi[c] : o->phi[n];
-          s = s + k8(dx, dy, dz) * v;
+          b[BLK(dx, dy, dz)] = (nflag_of(o, n) == OBST) ? o->phi[c] : o->phi[n];
         }
-    o->phis[c] = s / wsum;
+    o->phis[c] = k8_smooth(b);
   }
   /* Parker-Youngs normal n = grad(phi~) and n^ = n/|n| (R17) */
   for (c = 0; c < N; ++c) {
@@ -593,35 +653,13 @@ static void geometry(orc* o) {
     int a;
     if (o->flag[c] == OBST) continue;
     coords(o, c, &x, &y, &z);
-    for (a = 0; a < 3; ++a) {
-      double s = 0.0;
-      int p, r;
-      for (p = -1; p <= 1; ++p)
-        for (r = -1; r <= 1; ++r) {
-          int d1[3], d2[3];
-          long np, nm;
-          double vp, vm, w;
-          /* p runs over the slower, r over the faster of the two other axes */
-          if (a == 0) {
-            d1[0] = 1; d1[1] = r; d1[2] = p;
-          } else if (a == 1) {
-            d1[0] = r; d1[1] = 1; d1[2] = p;
-          } else {
-            d1[0] = r; d1[1] = p; d1[2] = 1;
-          }
-          d2[0] = d1[0];
-          d2[1] = d1[1];
-          d2[2] = d1[2];
-          d2[a] = -1;
-          np = nbr(o, x, y, z, d1[0], d1[1], d1[2]);
-          nm = nbr(o, x, y, z, d2[0], d2[1], d2[2]);
-          vp = (nflag_of(o, np) == OBST) ? o->phis[c] : o->phis[np];
-          vm = (nflag_of(o, nm) == OBST) ? o->phis[c] : o->phis[nm];
-          w = (p == 0 && r == 0) ? 4.0 : (p == 0 || r == 0) ? 2.0 : 1.0;
-          s = s + w * (vp - vm);
+    for (dz = -1; dz <= 1; ++dz)
+      for (dy = -1; dy <= 1; ++dy)
+        for (dx = -1; dx <= 1; ++dx) {
+          long n = nbr(o, x, y, z, dx, dy, dz);
+          b[BLK(dx, dy, dz)] = (nflag_of(o, n) == OBST) ? o->phis[c] : o->phis[n];
         }
-      n3[a] = s;
-    }
+    py_gradient(b, n3);
     len = sqrt(n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2]);
     for (a = 0; a < 3; ++a) o->nhat[a * N + c] = (len > 0.0) ? n3[a] / len : 0.0;
   }

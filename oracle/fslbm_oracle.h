@@ -73,6 +73,12 @@ void orc_select(int q, int variant, int om3_fallback, const double* nhat,
  * fstar_x[q] post-collision PDFs of the cell itself. */
 void orc_reconstruct(int q, const int* recon, double rho_g, const double* u,
                      const double* fstar_x, double* fin);
+/* Geometry stencils on one 3x3x3 block b[(dx+1) + 3 (dy+1) + 9 (dz+1)]:
+ * the K8-smoothed value at its centre (reading R16) and the raw
+ * Parker-Youngs gradient there (Eq. nm-fslbm-normal, reading R17; n3[3],
+ * not normalised).  The step's geometry evaluates every cell with them. */
+double orc_k8_smooth(const double* block27);
+void orc_py_gradient(const double* block27, double* n3);
 
 #ifdef __cplusplus
 }

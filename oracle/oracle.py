@@ -68,6 +68,9 @@ def _load():
         lib.orc_collide.argtypes = [i, i, d, d, p, p, p, p]
         lib.orc_select.argtypes = [i, i, i, p, p, p]
         lib.orc_reconstruct.argtypes = [i, p, d, p, p, p]
+        lib.orc_k8_smooth.restype = d
+        lib.orc_k8_smooth.argtypes = [p]
+        lib.orc_py_gradient.argtypes = [p, p]
         _lib = lib
         return lib
 
@@ -124,6 +127,22 @@ def reconstruct(q: int, recon, rho_g: float, u, fstar_x, fin) -> np.ndarray:
     fstar_x = np.ascontiguousarray(fstar_x, np.float64)
     out = np.array(fin, np.float64, copy=True)
     lib.orc_reconstruct(q, _ptr(recon), float(rho_g), _ptr(u), _ptr(fstar_x), _ptr(out))
+    return out
+
+
+def k8_smooth(block) -> float:
+    """K8-smoothed value at the centre of a 3x3x3 block (indexed [dz, dy, dx])."""
+    lib = _load()
+    b = np.ascontiguousarray(block, np.float64).reshape(27)
+    return float(lib.orc_k8_smooth(_ptr(b)))
+
+
+def py_gradient(block) -> np.ndarray:
+    """Raw Parker-Youngs gradient at the centre of a 3x3x3 block ([dz, dy, dx])."""
+    lib = _load()
+    b = np.ascontiguousarray(block, np.float64).reshape(27)
+    out = np.zeros(3, np.float64)
+    lib.orc_py_gradient(_ptr(b), _ptr(out))
     return out
 
 

@@ -538,6 +538,12 @@ __global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) k_geometry(DPtrs d, 
 #endif
 
 constexpr int kIfaceChunk = FSLBM_IFACE_CHUNK;
+// Half-width of the band of n^.c_i values that count as a tie n.c_i = 0
+// (Appendix A assumes that only c_0 ties; at mirror planes of the interface
+// a component of n^ is zero in exact arithmetic and rounding-sized in any
+// precision, so the sign alone would decide by rounding).  Exact in FP32
+// and FP64 alike.
+constexpr double kTie = 0x1p-20;
 constexpr int kIfaceMinBlocks = FSLBM_IFACE_MINB;
 // Pull with the free-surface BC (Eq. nm-fslbm-boundary-condition) on the
 // variant's set R (Sec. 3), mass exchange (Eq. nm-fslbm-mass-flux) with
@@ -648,17 +654,19 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     const R ux = jx / rc - R(0.5) * R(p.g[0]);
     const R uy = jy / rc - R(0.5) * R(p.g[1]);
     const R uz = jz / rc - R(0.5) * R(p.g[2]);
-    // set R of the variant (Sec. 3) and reconstruction
+    // set R of the variant (Sec. 3) and reconstruction; |n^.c_i| <= kTie
+    // counts as a tie (n.c_i = 0): NBRC reconstructs ties, NBKC does not
     const R n0 = nhat[3LL * c], n1 = nhat[3LL * c + 1], n2 = nhat[3LL * c + 2];
     int v = p.variant;
     if (v == 4) v = (__popc(miss) >= 3) ? 3 : p.om3_fb;
     const R rg = rhog[c];  // rho^G (FP64 engine) or rho^G - 1
+    const R tie = R(kTie);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       bool rec = (miss >> i) & 1u;
       const R dot = R(CX(i)) * n0 + R(CY(i)) * n1 + R(CZ(i)) * n2;
-      if (v == 1 && dot >= R(0.0)) rec = true;
-      if (v == 2 && dot > R(0.0)) rec = true;
+      if (v == 1 && dot >= -tie) rec = true;
+      if (v == 2 && dot > tie) rec = true;
       if (rec) {
         const int j = OPP(i);
         if constexpr (S::kDev) {

@@ -2,8 +2,9 @@
 
 The FP64 kernels keep the oracle's expression order and are compiled without
 FMA contraction; the bar is identical cell flags after every step and PDFs,
-fill levels and interface masses within 1e-12 relative (absolute 1e-12 for
-values below 1).  Inputs come from the seeded generators in
+fill levels and interface masses within 1e-12 relative: |gpu - oracle| <=
+1e-12 |oracle|, so a value the oracle holds as exactly 0 must be 0 on the GPU
+too.  Inputs come from the seeded generators in
 ``paper_2207_13962_gb300.scenarios``; nothing here is produced by the GPU.
 """
 import numpy as np
@@ -27,7 +28,7 @@ def _pair(sc, precision="FP64", **over):
 
 
 def _close(a, b, tol=TOL):
-    return np.abs(a - b) <= tol * np.maximum(1.0, np.abs(b))
+    return np.abs(a - b) <= tol * np.abs(b)
 
 
 def _compare(o, g, step, pdf=True):

@@ -9,25 +9,23 @@ M = sum of liquid PDFs + interface masses in FP64.
 
 Bars:
 * FP64 storage: the error is below 1e-12 (it is the parity mode).
-* FP32 storage (deviations f - w_i, FP32 arithmetic), variants OM and OM3:
-  amplitude within 1e-3 of a(0) (the stated observable bar).
-* NBRC and NBKC choose their reconstructed set by the sign of n.c_i.  The
-  crest column x = 0 is a mirror plane of the wave, so there n_x is a
-  rounding-sized number of either sign in FP64 and FP32 alike, and the two
-  runs reconstruct different sets there every step: their amplitude differs
-  by tens of percent although both are valid evaluations of the method.
-  Their error is printed, not bounded; cell-by-cell FP32 agreement of the
-  shared arithmetic is tested on OM (test_gpu_fp32.py).
+* FP32 storage (deviations f - w_i, FP32 arithmetic), all four variants:
+  amplitude within 1e-3 of a(0), the stated observable bar.  NBRC and NBKC
+  choose their reconstructed set by the sign of n.c_i; at the wave's mirror
+  columns n_x is zero in exact arithmetic, and the tie band of reading R5
+  (|n^.c_i| <= 2^-20 is a tie) makes FP32 and FP64 take the same decision
+  there instead of one decided by rounding.
 * Mass drift, FP32: every step rounds each of the q stored deviations of a
   cell once (|rounding| <= 2^-24 max|d|, max|d| <= w_0 (|rho - 1| + 3|u|)
   <= 1/3 x 1e-3 here), so the relative drift is at most 19 x 2^-24 x 3.3e-4
   = 3.8e-10 per step even when all cells round the same way: 3.8e-7 over
   1000 steps.  The measured drift is printed; it is ~1.6e-8 (correlated
-  rounding of a near-uniform state), above the 1e-10 aimed at.
-* FP16 / BF16 storage (deviations, FP32 arithmetic): the errors and the
-  drift are printed; the bound asserted is the format's own resolution,
-  2^-11 (FP16) / 2^-8 (BF16) of a(0) per step accumulated over a random walk
-  of 1000 steps, i.e. sqrt(1000) x 2^-11 = 1.5e-2 and 0.12.
+  rounding of a near-uniform state), above the 1e-10 aimed at; the
+  mass-exact storage modes are tested against 1e-10 in test_gpu_mass.py.
+* FP16 / BF16 storage (deviations, FP32 arithmetic): the amplitude error is
+  held to the same 1e-3 bar.  BF16 keeps 8 significant bits of a deviation
+  (FP16 with the 2^15 scale keeps 11), and its error is reported as an
+  expected failure when it misses the bar.
 """
 import numpy as np
 import pytest
@@ -101,11 +99,16 @@ def test_fp32_observables(variant, gpu_lib):
 @pytest.mark.parametrize("variant", ["NBRC", "NBKC"])
 def test_fp32_normal_set_variants(variant, gpu_lib):
     err, drift = _errors(variant, "FP32")
-    assert np.isfinite(err)
+    assert err <= 1e-3, err
     assert drift <= 3.8e-7, drift
 
 
-@pytest.mark.parametrize("precision,bound", [("FP16S", 1.5e-2), ("BF16S", 0.12)])
-def test_16bit_storage_observables(precision, bound, gpu_lib):
-    err, drift = _errors("OM", precision)
-    assert err <= bound, err
+def test_fp16_storage_observables(gpu_lib):
+    err, drift = _errors("OM", "FP16S")
+    assert err <= 1e-3, err
+
+
+def test_bf16_storage_observables(gpu_lib):
+    err, drift = _errors("OM", "BF16S")
+    if err > 1e-3:
+        pytest.xfail(f"BF16 deviation storage misses the 1e-3 observable bar: amplitude error {err:.3e} of a(0)")

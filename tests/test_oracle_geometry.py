@@ -96,3 +96,66 @@ def test_sphere_normal_direction_and_curvature(liquid_inside):
     k = kappa[shell]
     expect = (2.0 / r[shell]) * (1.0 if liquid_inside else -1.0)
     assert np.abs(np.mean(k) - np.mean(expect)) < 0.1 * 2.0 / R
+
+
+# ---------------------------------------------------------------------------
+# Exact weights of the stencils (readings R16, R17), pinned by their impulse
+# responses stored in tests/golden/.  Any other kernel shape, radius or
+# normalisation, or other difference weights, changes these values.
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        return json.load(fh)
+
+
+def test_k8_impulse_response_on_a_block():
+    from fractions import Fraction
+
+    from oracle import k8_smooth
+    g = _golden("k8_impulse.json")
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                b = np.zeros((3, 3, 3))
+                b[oz + 1, oy + 1, ox + 1] = 1.0
+                num, den = g["by_r2"][str(ox * ox + oy * oy + oz * oz)]
+                # the weight and its sum are exact dyadic numbers, so the
+                # one division rounds correctly: the result is exact to the
+                # last bit
+                assert k8_smooth(b) == float(Fraction(num, den)), (ox, oy, oz)
+
+
+def test_k8_impulse_response_in_a_domain():
+    """The step's smoothing of a fill-level impulse (one interface cell with
+    phi = 1 among gas cells, periodic 5^3 domain)."""
+    from fractions import Fraction
+    g = _golden("k8_impulse.json")
+    n = 5
+    o = Oracle(n, n, n, periodic=(True, True, True))
+    fill = np.zeros(n ** 3)
+    flags = np.zeros(n ** 3, np.uint8)
+    c = 2 + n * (2 + n * 2)
+    fill[c], flags[c] = 1.0, 1
+    o.init(fill, flags, None, None)
+    _, _, phis = o.geometry()
+    phis = phis.reshape(n, n, n)
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                r2 = (x - 2) ** 2 + (y - 2) ** 2 + (z - 2) ** 2
+                want = float(Fraction(*g["by_r2"][str(r2)])) if r2 <= 3 else 0.0
+                assert phis[z, y, x] == want, (x, y, z)
+
+
+def test_parker_youngs_impulse_response():
+    from oracle import py_gradient
+    g = _golden("parker_youngs_impulse.json")
+    assert len(g["cases"]) == 27
+    for case in g["cases"]:
+        ox, oy, oz = case["offset"]
+        b = np.zeros((3, 3, 3))
+        b[oz + 1, oy + 1, ox + 1] = 1.0
+        np.testing.assert_array_equal(py_gradient(b), np.array(case["gradient"], np.float64),
+                                      err_msg=str(case["offset"]))

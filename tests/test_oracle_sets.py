@@ -86,9 +86,9 @@ def test_set_invariants(q):
             np.testing.assert_array_equal(R["OM"], G)
             assert R["NBRC"][0] and not R["NBKC"][0] and not R["OM"][0]
             assert np.all(R["NBRC"] >= R["NBKC"])
-            # NBRC and NBKC differ only in ties n.c_i == 0
+            # NBRC and NBKC differ only in ties |n.c_i| <= 2^-20 (reading R5)
             diff = R["NBRC"] & ~R["NBKC"]
-            assert np.all(dots[diff] == 0.0)
+            assert np.all(np.abs(dots[diff]) <= 2.0 ** -20)
             # generic normal: exactly one of i, ibar lies in the normal half-space
             if np.all(dots[1:] != 0.0):
                 half = dots > 0
@@ -227,3 +227,28 @@ def test_force_balance_at_rest_normal_based(q):
             fin = reconstruct(q, R, rho_g, np.zeros(3), fstar, np.zeros(q))
             F = _force(c, n, np.zeros(3), K, R, fstar, fin)
             np.testing.assert_allclose(F, -n * rho_g * CS2, atol=1e-14)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_tie_band(q):
+    """Reading R5: a direction with |n^.c_i| <= 2^-20 is a tie.  NBRC
+    reconstructs it, NBKC only when it is missing; just outside the band the
+    sign of n^.c_i decides."""
+    c, _, _ = lattice(q)
+    c = c.astype(np.float64)
+    none = np.zeros(q, np.int32)
+    for eps, tie in ((0.0, True), (1e-9, True), (-1e-9, True), (2.0 ** -20, True),
+                     (3e-6, False), (-3e-6, False)):
+        n = np.array([eps, 1.0, 0.0])
+        n /= np.linalg.norm(n)
+        dots = c @ n
+        nbrc = select(q, V["NBRC"], V["NBKC"], n, none)
+        nbkc = select(q, V["NBKC"], V["NBKC"], n, none)
+        for i in range(q):
+            if tuple(c[i]) in ((1, 0, 0), (-1, 0, 0), (1, 0, 1), (-1, 0, -1)):
+                assert abs(dots[i]) <= 3e-6
+                assert nbrc[i] == (tie or dots[i] > 0), (eps, i)
+                assert nbkc[i] == (not tie and dots[i] > 0), (eps, i)
+        miss = none.copy()
+        miss[[i for i in range(q) if tuple(c[i]) == (1, 0, 0)][0]] = 1
+        assert select(q, V["NBKC"], V["NBKC"], n, miss)[miss.astype(bool)].all()
