@@ -35,8 +35,10 @@ if ROOT not in sys.path:
 
 METRIC = "FSLBM MLUPS and % HBM roofline on 1 GB300; batched/served vs plain at stated error; p50/p99"
 Q = 19
-S_BYTES = {"FP32": 4, "FP64": 8, "FP16S": 2, "BF16S": 2}
-DTYPE = {"FP32": "f32", "FP64": "f64", "FP16S": "f32 (fp16 storage)", "BF16S": "f32 (bf16 storage)"}
+S_BYTES = {"FP32": 4, "FP64": 8, "FP16S": 2, "BF16S": 2, "FP32MC": 4, "FP16SMC": 2}
+REST_BYTES = {"FP32MC": 8, "FP16SMC": 8}  # the FP64 rest slice of the mass-conserving formats
+DTYPE = {"FP32": "f32", "FP64": "f64", "FP16S": "f32 (fp16 storage)", "BF16S": "f32 (bf16 storage)",
+         "FP32MC": "f32 (f32 storage, f64 rest)", "FP16SMC": "f32 (fp16 storage, f64 rest)"}
 
 
 # ------------------------------------------------------------------ helpers
@@ -199,10 +201,25 @@ def oracle_sample(sc, name: str, zlo: int, zhi: int):
     return S.z_slab(sc, zlo, zhi)
 
 
-def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50):
-    """Oracle MLUPS on a bounded sample of the workload (single host thread)."""
+def _time_oracle(smp, steps_budget_s, max_steps, openmp=False, warmup=1):
     from oracle import Oracle
     from paper_2207_13962_gb300 import scenarios as S
+    o = Oracle(*smp.shape, **S.make_oracle_kwargs(smp), openmp=openmp)
+    o.init(smp.fill, smp.flags, smp.velocity, smp.density)
+    o.step(warmup)
+    done, t0 = 0, time.perf_counter()
+    while done < max_steps:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > steps_budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50, openmp=False):
+    """Oracle MLUPS on a bounded sample of the workload: one host thread, or
+    all host threads with the OpenMP build (its per-cell geometry and
+    stream-collide loops shared out)."""
     if name == "taylor_bubble":
         smp = oracle_sample(sc, name, 352, 416)
     elif name == "taylor_bubble_256":
@@ -211,20 +228,37 @@ def run_oracle_sample(sc, name, steps_budget_s=15.0, max_steps=50):
         smp = oracle_sample(sc, name, sc.shape[2] - 64, sc.shape[2])
     else:
         smp = sc
-    o = Oracle(*smp.shape, **S.make_oracle_kwargs(smp))
-    o.init(smp.fill, smp.flags, smp.velocity, smp.density)
-    o.step(1)
-    done, t0 = 0, time.perf_counter()
-    while done < max_steps:
-        o.step(1)
-        done += 1
-        if time.perf_counter() - t0 > steps_budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": smp.N * done / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    done, dt = _time_oracle(smp, steps_budget_s, max_steps, openmp=openmp)
+    cores = (os.cpu_count() or 1) if openmp else 1
+    threads = f"{cores} host threads (OpenMP build)" if openmp else "1 host thread"
+    return {"value": smp.N * done / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"{smp.name}: {smp.shape[0]}x{smp.shape[1]}x{smp.shape[2]} cells of the same "
-                      f"initial state, {done} steps after 1 warm-up step, FP64, 1 host thread",
+                      f"initial state, {done} steps after 1 warm-up step, FP64, {threads}",
             "seconds": dt}
+
+
+def cpu_baseline_set(sc, name):
+    """The oracle timed on the host: the workload's bounded sample on one
+    thread (the headline value) and on all threads, the standing gravity wave
+    in full (1000 steps, one thread) and the first steps of the rectangular
+    dam break on all threads; core counts stated with each."""
+    from paper_2207_13962_gb300 import scenarios as S
+    out = run_oracle_sample(sc, name)
+    out.pop("seconds", None)
+    omp = run_oracle_sample(sc, name, steps_budget_s=8.0, openmp=True)
+    omp.pop("seconds", None)
+    out["all_cores"] = omp
+    wave = S.gravity_wave(variant="OM")
+    done, dt = _time_oracle(wave, 60.0, 1000, warmup=0)
+    out["gravity_wave_32x64x1"] = {"value": wave.N * done / dt / 1e6, "unit": "MLUPS", "cores": 1,
+                                   "sample": f"all {done} steps of the 32x64x1 gravity wave, FP64, 1 host thread"}
+    dam = S.dam_break(variant="OM")
+    done, dt = _time_oracle(dam, 10.0, 500, openmp=True, warmup=0)
+    out["dam_break_256x128x64"] = {"value": dam.N * done / dt / 1e6, "unit": "MLUPS",
+                                   "cores": os.cpu_count() or 1,
+                                   "sample": f"first {done} steps of the 256x128x64 dam break, FP64, "
+                                             f"{os.cpu_count()} host threads (OpenMP build)"}
+    return out
 
 
 # -------------------------------------------------------------- our arm
@@ -283,7 +317,7 @@ def bench_ours(args, ws, rank, local):
     n_liq = 0.5 * (obs1["n_liquid"] + obs2["n_liquid"])
     # algorithmic bytes of one bulk launch: read + write q PDFs and read one
     # flag byte per liquid cell (the sweep visits liquid cells only)
-    alg_bytes = n_liq * (2 * Q * S_BYTES[prec] + 1)
+    alg_bytes = n_liq * (2 * ((Q - (1 if prec in REST_BYTES else 0)) * S_BYTES[prec] + REST_BYTES.get(prec, 0)) + 1)
     achieved = alg_bytes / (bulk_ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -333,12 +367,17 @@ def bench_ours(args, ws, rank, local):
             "note": "L2 not flushed: the touched state (~40 MB) fits in L2"}
         c2.close()
 
+    batched = served = None
+    if args.workload == "taylor_bubble" and not args.no_secondary and ws == 1:
+        ctx.close()
+        batched = bench_batch(args, emit=False)
+        served = bench_serve(args, emit=False)
+
     line = None
     if rank == 0:
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
-            cpu = run_oracle_sample(sc, args.workload)
-            cpu.pop("seconds", None)
+            cpu = cpu_baseline_set(sc, args.workload)
         line = {
             "metric": METRIC,
             "value": round(value, 2),
@@ -378,6 +417,8 @@ def bench_ours(args, ws, rank, local):
             "gpu_launches": int(launches),
             "clocks": ck,
             "other_workloads": other,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -406,11 +447,12 @@ def _crown(fill, flags, L):
     return float(top + f3[top][flags.reshape(L, L, L)[top] == S.IFACE].max())
 
 
-def bench_batch(args):
-    """64 cylindrical dam breaks of seeded uneven sizes (D3Q27 TRT): as one
-    batch in FP32 and in reduced precision, and one at a time in plain FP32.
-    Every run is brought to the same step count, so the front radii compare
-    at the same time."""
+def bench_batch(args, emit=True):
+    """64 cylindrical dam breaks of seeded uneven sizes (D3Q27 TRT): one at a
+    time in plain FP32, as one batch in FP32 and as one batch in the reduced
+    (by default mass-conserving FP16) storage.  Every run is brought to the
+    same step count, so the front radii compare at the same time; the error
+    is relative to the plain FP32 runs."""
     import torch
     from paper_2207_13962_gb300 import fslbm
     from paper_2207_13962_gb300 import scenarios as S
@@ -419,6 +461,7 @@ def bench_batch(args):
     scs = [S.cylinder_dam_break(**p, q=27) for p in prm]
     cells = sum(sc.N for sc in scs)
     steps = args.batch_steps
+    total = args.batch_warmup + steps
     stream = torch.cuda.Stream()
 
     def timed(fn):
@@ -434,24 +477,7 @@ def bench_batch(args):
         return [(_front_radius(c.read(pdf=False)["fill"], sc.shape[0]), c.observables()["total_mass"])
                 for sc, c in zip(scs, ctxs)]
 
-    res, obs_at, total = {}, {}, None
-    for prec in ("FP32", args.batch_precision):
-        ctxs = [fslbm.context_for(sc, precision=prec, stream=stream.cuda_stream) for sc in scs]
-        m0 = [c.observables()["total_mass"] for c in ctxs]
-        batch = fslbm.Batch(ctxs, stream=stream.cuda_stream)
-        tune = batch.autotune(steps=1) if args.autotune else batch.tuning()
-        done = ctxs[0].observables()["step"]
-        if total is None:
-            total = max(done, args.warmup) + steps
-        batch.step(total - steps - done)
-        t = timed(lambda: batch.step(steps))
-        obs_at[prec] = observe(ctxs)
-        res[f"batched_{prec.lower()}"] = {
-            "mlups": cells * steps / t / 1e6, "seconds": t, "tuning": tune, "launches": batch.launches(),
-            "mass_drift_rel_max": max(abs(o[1] - m) / m for o, m in zip(obs_at[prec], m0))}
-        batch.close()
-        for c in ctxs:
-            c.close()
+    res, obs_at = {}, {}
     # plain: each domain alone, one after another, FP32
     ctxs = [fslbm.context_for(sc, precision="FP32", stream=stream.cuda_stream) for sc in scs]
     m0 = [c.observables()["total_mass"] for c in ctxs]
@@ -459,92 +485,145 @@ def bench_batch(args):
         c.step(total - steps)
     t = timed(lambda: [c.step(steps) for c in ctxs])
     ref = observe(ctxs)
-    res["plain_fp32"] = {"mlups": cells * steps / t / 1e6, "seconds": t,
+    res["plain_fp32"] = {"mlups": round(cells * steps / t / 1e6, 1), "seconds": round(t, 4),
                          "mass_drift_rel_max": max(abs(o[1] - m) / m for o, m in zip(ref, m0))}
     for c in ctxs:
         c.close()
-    for prec, obs in obs_at.items():
-        res[f"batched_{prec.lower()}"]["front_radius_rel_err_vs_plain_fp32"] = max(
-            abs(a[0] - b[0]) / max(b[0], 1e-30) for a, b in zip(obs, ref))
-    line = {"metric": METRIC, "workload": "batched cylindrical dam breaks",
-            "config": {"domains": len(scs), "cells": cells, "lattice": "D3Q27", "collision": "TRT",
-                       "sides": [p["L"] for p in prm], "timed_steps": steps, "steps_total": total,
-                       "seed": 2207, "g": 1e-5, "nu": 1e-3, "variant": "OM"},
-            "unit": "MLUPS", "results": res, "data": "synthetic (seeded generator, no dataset)"}
-    print(json.dumps(line), flush=True)
-    return line
+    for prec in ("FP32", args.batch_precision):
+        ctxs = [fslbm.context_for(sc, precision=prec, stream=stream.cuda_stream) for sc in scs]
+        m0 = [c.observables()["total_mass"] for c in ctxs]
+        batch = fslbm.Batch(ctxs, stream=stream.cuda_stream)
+        tune = batch.autotune(steps=1) if args.autotune else batch.tuning()
+        done = ctxs[0].observables()["step"]
+        batch.step(max(0, total - steps - done))
+        l0 = batch.launches()
+        t = timed(lambda: batch.step(steps))
+        obs_at[prec] = observe(ctxs)
+        res[f"batched_{prec.lower()}"] = {
+            "mlups": round(cells * steps / t / 1e6, 1), "seconds": round(t, 4), "tuning": tune,
+            "launches_per_step": (batch.launches() - l0) / steps,
+            "mass_drift_rel_max": max(abs(o[1] - m) / m for o, m in zip(obs_at[prec], m0)),
+            "front_radius_rel_err_vs_plain_fp32": max(abs(a[0] - b[0]) / max(b[0], 1e-30)
+                                                      for a, b in zip(obs_at[prec], ref))}
+        batch.close()
+        for c in ctxs:
+            c.close()
+    out = {"workload": f"{len(scs)} cylindrical dam breaks, cubes of seeded sides "
+                       f"{min(p['L'] for p in prm)}..{max(p['L'] for p in prm)} (seed 2207), D3Q27 TRT, "
+                       f"g=1e-5, nu=1e-3, OM; {steps} timed steps after {total - steps}",
+           "cells": cells, "unit": "MLUPS", "results": res,
+           "observable": "front radius sqrt(sum of floor-layer fill / pi), relative to the plain FP32 runs"}
+    if emit:
+        print(json.dumps({"metric": METRIC, "workload": "batched cylindrical dam breaks", **out,
+                          "data": "synthetic (seeded generator, no dataset)"}), flush=True)
+    return out
 
 
-def bench_serve(args):
+def _serve_trace(scs, steps, submit_fn, poll_fn):
+    """Replays an arrival trace in real time through a server; returns the
+    results by trace index and the makespan (first arrival to last result)."""
+    pending = list(range(len(scs)))
+    ids, results = {}, {}
+    t0 = time.perf_counter()
+    while len(results) < len(scs):
+        now = time.perf_counter() - t0
+        while pending and scs[pending[0]][0] <= now:
+            k = pending.pop(0)
+            ids[submit_fn(scs[k][1], steps)] = k
+        if not ids and pending:
+            time.sleep(max(0.0, scs[pending[0]][0] - (time.perf_counter() - t0)))
+            continue
+        for rid, r in poll_fn():
+            results[ids.pop(rid)] = r
+    return results, time.perf_counter() - t0
+
+
+def bench_serve(args, emit=True):
     """Drop impacts arriving as a Poisson stream (mean 20 req/s, seeded sizes
-    96..256): a FIFO one-at-a-time plain FP32 server (simulated on the
-    measured run times) against the continuous-batching server in FP32 and
-    in reduced precision, replayed in real time."""
+    96..256), replayed in real time: a FIFO server that runs each request
+    alone in plain FP32, one after another, against the continuous-batching
+    server in FP32 and in the reduced (by default mass-conserving FP16)
+    storage.  Time-to-result runs from a request's arrival to its result on
+    the host; the crown-height error is relative to the plain FP32 run."""
     import torch
     from paper_2207_13962_gb300 import fslbm
     from paper_2207_13962_gb300 import scenarios as S
     torch.cuda.set_device(0)
-    trace = S.drop_requests(n=args.requests)
+    trace = S.drop_requests(n=args.requests, rate=args.rate)
     scs = [(t, S.drop_impact(**kw)) for t, kw in trace]
     steps = args.serve_steps
     cells = sum(sc.N for _, sc in scs)
     out = {}
-    # plain: each request alone in arrival order; time-to-result includes
-    # the wait behind earlier requests (FIFO, one at a time)
-    run_s, ref = [], []
-    for _, sc in scs:
-        c = fslbm.context_for(sc, precision="FP32")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        c.step(steps)
-        c.sync()
-        run_s.append(time.perf_counter() - t0)
-        r = c.read(pdf=False)
-        ref.append((_crown(r["fill"], r["flags"], sc.shape[0]), c.observables()["total_mass"]))
-        c.close()
-    clock, ttr = 0.0, []
-    for (arr, _), rs in zip(scs, run_s):
-        clock = max(clock, arr) + rs
-        ttr.append(clock - arr)
-    out["plain_fp32_fifo"] = {"mlups": cells * steps / sum(run_s) / 1e6, "busy_seconds": sum(run_s),
-                              "p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
-                              "makespan_s": clock}
+
+    # FIFO, one at a time, plain FP32 contexts
+    queue = []
+
+    def fifo_submit(sc, n):
+        queue.append((len(queue), sc, time.perf_counter()))
+        return len(queue) - 1
+
+    def fifo_poll():
+        done = []
+        while queue and not done:
+            k, sc, t_sub = queue.pop(0)
+            c = fslbm.context_for(sc, precision="FP32")
+            M0 = c.observables()["total_mass"]
+            c.step(steps)
+            c.sync()
+            r = c.read(pdf=False)
+            obs = c.observables()
+            c.close()
+            done.append((k, {"t_result": time.perf_counter() - t_sub, "fill": r["fill"], "flags": r["flags"],
+                             "drift": abs(obs["total_mass"] - M0) / M0}))
+        return done
+
+    res, makespan = _serve_trace(scs, steps, fifo_submit, fifo_poll)
+    ref = [_crown(res[k]["fill"], res[k]["flags"], scs[k][1].shape[0]) for k in range(len(scs))]
+    ttr = [res[k]["t_result"] for k in range(len(scs))]
+    out["plain_fp32_fifo"] = {"mlups": round(cells * steps / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
+                              "p50_s": round(float(np.percentile(ttr, 50)), 4),
+                              "p99_s": round(float(np.percentile(ttr, 99)), 4),
+                              "mass_drift_rel_max": max(res[k]["drift"] for k in res)}
     for prec in ("FP32", args.batch_precision):
         srv = fslbm.Server(q=19, precision=prec, max_active=args.max_active, chunk_steps=args.chunk_steps)
-        pending = list(range(len(scs)))
-        ids, results = {}, {}
-        t0 = time.perf_counter()
-        while len(results) < len(scs):
-            now = time.perf_counter() - t0
-            while pending and scs[pending[0]][0] <= now:
-                k = pending.pop(0)
-                ids[srv.submit(scs[k][1], steps)] = k
-            if srv.stats()["active"] == 0 and srv.stats()["queued"] == 0 and pending:
-                time.sleep(max(0.0, scs[pending[0]][0] - (time.perf_counter() - t0)))
-                continue
+        m0 = {}
+
+        def submit(sc, n):
+            rid = srv.submit(sc, n)
+            m0[rid] = None
+            return rid
+
+        def poll():
             srv.poll()
-            for rid, k in list(ids.items()):
+            got = []
+            for rid in list(m0):
                 r = srv.result(rid)
                 if r is not None:
-                    results[k] = r
-                    del ids[rid]
-        makespan = time.perf_counter() - t0
-        ttr = [results[k]["t_result"] for k in range(len(scs))]
-        err = max(abs(_crown(results[k]["fill"], results[k]["flags"], scs[k][1].shape[0]) - ref[k][0]) /
-                  max(ref[k][0], 1e-30) for k in range(len(scs)))
+                    del m0[rid]
+                    got.append((rid, r))
+            return got
+
+        res, makespan = _serve_trace(scs, steps, submit, poll)
+        ttr = [res[k]["t_result"] for k in range(len(scs))]
+        err = max(abs(_crown(res[k]["fill"], res[k]["flags"], scs[k][1].shape[0]) - ref[k]) / max(ref[k], 1e-30)
+                  for k in range(len(scs)))
         st = srv.stats()
-        out[f"served_{prec.lower()}"] = {"mlups": cells * steps / makespan / 1e6, "makespan_s": makespan,
-                                         "p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
-                                         "crown_rel_err_vs_plain_fp32": err, "max_active_seen": st["max_active_seen"],
-                                         "batch_rebuilds": st["batch_rebuilds"]}
+        out[f"served_{prec.lower()}"] = {
+            "mlups": round(cells * steps / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
+            "p50_s": round(float(np.percentile(ttr, 50)), 4), "p99_s": round(float(np.percentile(ttr, 99)), 4),
+            "crown_rel_err_vs_plain_fp32": err, "max_active_seen": st["max_active_seen"],
+            "batch_rebuilds": st["batch_rebuilds"]}
         srv.close()
-    line = {"metric": METRIC, "workload": "served drop impacts (continuous batching)",
-            "config": {"requests": len(scs), "cells": cells, "steps_per_request": steps, "rate_per_s": 20.0,
-                       "seed": 13962, "sides": [sc.shape[0] for _, sc in scs], "max_active": args.max_active,
-                       "chunk_steps": args.chunk_steps, "lattice": "D3Q19", "collision": "TRT", "variant": "OM"},
-            "unit": "MLUPS", "results": out, "data": "synthetic (seeded generator, no dataset)"}
-    print(json.dumps(line), flush=True)
-    return line
+    summary = {"workload": f"{len(scs)} drop impacts of seeded sides {min(sc.shape[0] for _, sc in scs)}.."
+                           f"{max(sc.shape[0] for _, sc in scs)} (seed 13962), Poisson arrivals {args.rate}/s, "
+                           f"{steps} steps each, D3Q19 TRT OM, replayed in real time",
+               "cells": cells, "unit": "MLUPS", "results": out, "max_active": args.max_active,
+               "chunk_steps": args.chunk_steps,
+               "observable": "crown height max over interface cells of (k + fill), relative to the plain FP32 run"}
+    if emit:
+        print(json.dumps({"metric": METRIC, "workload": "served drop impacts (continuous batching)", **summary,
+                          "data": "synthetic (seeded generator, no dataset)"}), flush=True)
+    return summary
 
 
 # --------------------------------------------------------- reference arm
@@ -639,7 +718,9 @@ def main(argv=None):
                     help="print the bulk sweep's sector counts on the workload's initial state (CPU only)")
     ap.add_argument("--batch-n", type=int, default=64, help="batch_cylinders: domains")
     ap.add_argument("--batch-steps", type=int, default=200, help="batch_cylinders: timed steps")
-    ap.add_argument("--batch-precision", default="FP16S", choices=["FP16S", "BF16S", "FP32"])
+    ap.add_argument("--batch-warmup", type=int, default=200, help="batch_cylinders: steps before the timed ones")
+    ap.add_argument("--batch-precision", default="FP16SMC", choices=["FP16SMC", "FP32MC", "FP16S", "BF16S", "FP32"])
+    ap.add_argument("--rate", type=float, default=20.0, help="serve_drops: mean arrivals per second")
     ap.add_argument("--autotune", action="store_true", help="batch_cylinders: autotune the launch shape")
     ap.add_argument("--requests", type=int, default=24, help="serve_drops: requests of the trace")
     ap.add_argument("--serve-steps", type=int, default=1000, help="serve_drops: steps per request")

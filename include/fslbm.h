@@ -73,12 +73,20 @@ typedef enum {
  * deviation d_i = f_i - w_i from the rest state (FP16 as d_i * 2^15) and
  * compute in FP32 on deviations, so that rounding is relative to |d| ~ 1e-3
  * rather than to |f|.  Fill level, mass, excess mass, the mass flux between
- * cells and bubble volumes are always FP64. */
+ * cells and bubble volumes are always FP64.
+ * FSLBM_FP32MC and FSLBM_FP16SMC are the mass-conserving forms of FP32 and
+ * FP16S: the q - 1 moving deviations lie on a fixed grid (2^-44 and 2^-39),
+ * the rest deviation is stored in FP64 and takes up every rounding of the
+ * collision, so each liquid cell keeps exactly the mass it received and the
+ * liquid mass (Eq. nm-fslbm-mass) does not drift with the storage rounding.
+ * They store 8 more bytes per cell and buffer than FP32 / FP16S. */
 typedef enum {
   FSLBM_FP64 = 0,
   FSLBM_FP32 = 1,
   FSLBM_FP16S = 2,
-  FSLBM_BF16S = 3
+  FSLBM_BF16S = 3,
+  FSLBM_FP32MC = 4,
+  FSLBM_FP16SMC = 5
 } fslbm_precision;
 
 typedef struct {
@@ -121,6 +129,21 @@ void fslbm_params_default(fslbm_params* p);
 fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
                           fslbm_collision collision, fslbm_bc_variant bc_variant,
                           const fslbm_params* params, fslbm_ctx** out);
+
+/* Storage order of the cells inside the context (a storage choice: results
+ * are the same for every order, bitwise in FP64).  The caller's cell index
+ * c = x + nx * (y + ny * z) of every host array in and out of the library
+ * never changes.  order[k] is the axis (0 x, 1 y, 2 z) held at storage
+ * position k, order[0] the contiguous one.  The bulk stream-collide sweeps
+ * 32-cell groups of consecutive storage positions, so it keeps more lanes
+ * busy when liquid runs are long along the contiguous axis (a tube along z
+ * wants z contiguous).  order == NULL (the default) lets fslbm_init choose:
+ * the axis with the fewest liquid-holding groups for the initial flags, x
+ * unless another axis needs at most 95 % of x's groups.  Takes effect at the
+ * next fslbm_init.  FSLBM_EINVAL unless order is a permutation of 0, 1, 2. */
+fslbm_status fslbm_set_axis_order(fslbm_ctx* ctx, const int* order);
+/* The storage order in use (order[3]); identity until the first init. */
+fslbm_status fslbm_get_axis_order(const fslbm_ctx* ctx, int* order);
 
 /* Initial state (Sec. 2.2).  fill[N] fill levels (used on interface cells;
  * liquid 1, gas 0), flags[N] cell types 0..3, velocity[3N] component-major
@@ -170,7 +193,10 @@ fslbm_status fslbm_set_timing(fslbm_ctx* ctx, int enable);
 fslbm_status fslbm_stage_times(fslbm_ctx* ctx, double* ms, int cap, int* n_launches);
 
 /* Checkpoint of the full state (PDFs, flags, fill, mass, bubbles, step) into
- * a caller buffer.  With buf == NULL only *size is returned. */
+ * a caller buffer.  With buf == NULL only *size is returned.  The arrays are
+ * kept in the context's storage order; fslbm_load accepts a checkpoint only
+ * in a context with the same sizes, lattice, precision, bubble count and
+ * storage order (FSLBM_EINVAL otherwise). */
 fslbm_status fslbm_save(fslbm_ctx* ctx, void* buf, size_t* size);
 fslbm_status fslbm_load(fslbm_ctx* ctx, const void* buf, size_t size);
 
@@ -189,16 +215,21 @@ fslbm_status fslbm_work_counts(fslbm_ctx* ctx, int64_t* interface_cells,
  * loop).  The paper has no counterpart: this is a service of the library.
  * Same results as fslbm_observables on the same state.
  *   domain: sizes (periodic flags unused); q: 19 or 27; g[3]: gravity (host).
- *   pdf: device, q*N FP64 post-collision PDFs, direction-major (stride N).
+ *   pdf: device, q*N FP64 post-collision PDFs, direction-major and unpadded:
+ *        PDF i of cell c at pdf[i * N + c] (contexts pad their own direction
+ *        slices, so pass an array like the one fslbm_read_fields returns).
  *   flags, fill, mass: device, N entries each (flags 0..3, higher bits ignored).
  *   out: host; stream: cudaStream_t or NULL.  Synchronizes the stream.
  * Allocates nothing: the block partials live in a fixed 66 KB device array
  * of the library (held by every GPU that loads it until the process exits).
- * The first call on a device looks up that array's device address; make it
- * before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialized by the caller.  FSLBM_EINVAL for q not 19/27, empty domains or
- * more than 2^31 - 1 cells; FSLBM_ECUDA if a CUDA call fails. */
+ * The first call on a device looks up that array's device address and keeps
+ * it for the life of the process; make that call before any stream capture.
+ * The kept address does not survive cudaDeviceReset: after a reset of the
+ * device in the same process, this entry point must not be used again.  All
+ * calls share the array, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialized by the caller.
+ * FSLBM_EINVAL for q not 19/27, empty domains or more than 2^31 - 1 cells;
+ * FSLBM_ECUDA if a CUDA call fails. */
 fslbm_status fslbm_observables_noalloc(const fslbm_domain* domain, int q, const double* g,
                                        const double* pdf, const uint8_t* flags,
                                        const double* fill, const double* mass,

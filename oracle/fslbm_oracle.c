@@ -630,13 +630,17 @@ static void py_gradient(const double* b, double* n3) {
 double orc_k8_smooth(const double* block27) { return k8_smooth(block27); }
 void orc_py_gradient(const double* block27, double* n3) { py_gradient(block27, n3); }
 
+/* The per-cell loops below (and those of classify() and stream_collide())
+ * write only their own cell's entries; built with -fopenmp they are shared
+ * out over threads with the same results. */
 static void geometry(orc* o) {
   long N = o->N, c;
-  int x, y, z, dx, dy, dz;
-  double b[27];
   /* smoothed fill level on every non-obstacle cell; obstacle and
    * out-of-domain stencil points take the centre's value */
+#pragma omp parallel for schedule(static)
   for (c = 0; c < N; ++c) {
+    int x, y, z, dx, dy, dz;
+    double b[27];
     if (o->flag[c] == OBST) continue;
     coords(o, c, &x, &y, &z);
     for (dz = -1; dz <= 1; ++dz)
@@ -648,9 +652,10 @@ static void geometry(orc* o) {
     o->phis[c] = k8_smooth(b);
   }
   /* Parker-Youngs normal n = grad(phi~) and n^ = n/|n| (R17) */
+#pragma omp parallel for schedule(static)
   for (c = 0; c < N; ++c) {
-    double n3[3], len;
-    int a;
+    double n3[3], len, b[27];
+    int a, x, y, z, dx, dy, dz;
     if (o->flag[c] == OBST) continue;
     coords(o, c, &x, &y, &z);
     for (dz = -1; dz <= 1; ++dz)
@@ -664,9 +669,10 @@ static void geometry(orc* o) {
     for (a = 0; a < 3; ++a) o->nhat[a * N + c] = (len > 0.0) ? n3[a] / len : 0.0;
   }
   /* curvature kappa = -div(n^) by central differences (R18) and rho^G (R7) */
+#pragma omp parallel for schedule(static)
   for (c = 0; c < N; ++c) {
     double s = 0.0, pv;
-    int a;
+    int a, x, y, z;
     if (o->flag[c] != IFACE) {
       o->kappa[c] = 0.0;
       o->rhog[c] = 0.0;
@@ -700,8 +706,9 @@ void orc_geometry(orc* o, double* nhat, double* kappa, double* phis) {
 /* Thuerey class of an interface cell (R12). */
 static void classify(orc* o) {
   long c;
-  int i, x, y, z;
+#pragma omp parallel for schedule(static)
   for (c = 0; c < o->N; ++c) {
+    int i, x, y, z;
     int has_l = 0, has_g = 0;
     o->cls[c] = STD;
     if (o->flag[c] != IFACE) continue;
@@ -731,10 +738,11 @@ static void stream_collide(orc* o) {
   const lattice* L = &o->L;
   const int q = L->q;
   long N = o->N, c;
-  int i, x, y, z;
+#pragma omp parallel for schedule(static)
   for (c = 0; c < N; ++c) {
     double fin[27], fout[27], fx[27], rho, u[3];
     int miss[27], recon[27];
+    int i, x, y, z;
     int fl = o->flag[c];
     if (fl != LIQ && fl != IFACE) continue;
     coords(o, c, &x, &y, &z);

@@ -18,34 +18,43 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fslbm_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 VARIANTS = {"NBRC": 1, "NBKC": 2, "OM": 3, "OM3": 4}
 
 
-def build_oracle(force: bool = False) -> str:
+def build_oracle(force: bool = False, openmp: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2,
-    -ffp-contract=off so that no multiply-add is fused)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(os.path.join(_HERE, "fslbm_oracle.h"))):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
+    -ffp-contract=off so that no multiply-add is fused).  ``openmp`` builds
+    ``liboracle_omp.so`` from the same source with -fopenmp: its
+    stream-collide cell loop runs on all host threads, for the CPU-baseline
+    timing only (the tests use the sequential library)."""
+    lib_path = _LIB_OMP if openmp else _LIB
+    os.makedirs(os.path.dirname(lib_path), exist_ok=True)
+    if (not force and os.path.exists(lib_path)
+            and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(lib_path) >= os.path.getmtime(os.path.join(_HERE, "fslbm_oracle.h"))):
+        return lib_path
+    tmp = lib_path + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu99", "-fPIC"]
+    cmd += ["-fopenmp"] if openmp else []
+    cmd += ["-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
-def _load():
-    global _lib
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is not None:
+        if openmp and _lib_omp is not None:
+            return _lib_omp
+        if not openmp and _lib is not None:
             return _lib
-        lib = C.CDLL(build_oracle())
+        lib = C.CDLL(build_oracle(openmp=openmp))
         d, i, p = C.c_double, C.c_int, C.c_void_p
         lib.orc_create.restype = p
         lib.orc_create.argtypes = [i, i, i, i, i, i, i, i, i, i, i, d, d, d, d, d, d, d, d]
@@ -71,7 +80,10 @@ def _load():
         lib.orc_k8_smooth.restype = d
         lib.orc_k8_smooth.argtypes = [p]
         lib.orc_py_gradient.argtypes = [p, p]
-        _lib = lib
+        if openmp:
+            _lib_omp = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -153,13 +165,15 @@ class Oracle:
     periodic flags, q (19/27), collision ('SRT'/'TRT'), variant
     ('NBRC'/'NBKC'/'OM'/'OM3'), OM3 fallback, bubble model, omega, TRT magic
     parameter, gravity g[3], surface tension sigma, eps_phi, p_v0.
+    ``openmp`` runs the stream-collide cell loop on all host threads (the
+    OpenMP build of the same source; same results).
     """
 
     def __init__(self, nx, ny, nz, periodic=(False, False, False), q=19, collision="TRT",
                  variant="OM", om3_fallback="NBKC", bubble_model=False, omega=1.0,
                  trt_magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), sigma=0.0, eps_phi=1e-2,
-                 p_v0=1.0 / 3.0):
-        self._lib = _load()
+                 p_v0=1.0 / 3.0, openmp=False):
+        self._lib = _load(openmp)
         self.shape = (int(nx), int(ny), int(nz))
         self.N = int(nx) * int(ny) * int(nz)
         self.q = int(q)

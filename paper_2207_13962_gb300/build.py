@@ -23,6 +23,7 @@ SOURCES = {
     "fslbm_f64.cu": ["--fmad=false"],
     "fslbm_f32.cu": [],
     "fslbm_f16.cu": [],
+    "fslbm_mc.cu": [],
     "fslbm_noalloc.cu": [],
     "fslbm_batch.cu": [],
     "fslbm_server.cu": [],

@@ -157,7 +157,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   if (N > 400LL * 1000 * 1000) return FSLBM_EINVAL;
   if (lattice != FSLBM_D3Q19 && lattice != FSLBM_D3Q27) return FSLBM_EINVAL;
   if (!valid_enum(collision, 0, 1) || !valid_enum(bc_variant, 1, 4)) return FSLBM_EINVAL;
-  if (!valid_enum(params->precision, 0, 3)) return FSLBM_EINVAL;
+  if (!valid_enum(params->precision, 0, 5)) return FSLBM_EINVAL;
   if (params->om3_fallback != FSLBM_NBRC && params->om3_fallback != FSLBM_NBKC) return FSLBM_EINVAL;
   if (!(params->omega > 0.0 && params->omega < 2.0)) return FSLBM_EINVAL;
   if (collision == FSLBM_TRT && !(params->trt_magic > 0.0)) return FSLBM_EINVAL;
@@ -175,7 +175,9 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
     case FSLBM_FP64: c->ops = ops_f64(c->q); break;
     case FSLBM_FP32: c->ops = ops_f32(c->q); break;
     case FSLBM_FP16S: c->ops = ops_f16s(c->q); break;
-    default: c->ops = ops_bf16s(c->q); break;
+    case FSLBM_BF16S: c->ops = ops_bf16s(c->q); break;
+    case FSLBM_FP32MC: c->ops = ops_f32mc(c->q); break;
+    default: c->ops = ops_f16smc(c->q); break;
   }
   KParams& k = c->kp;
   k.nx = domain->nx;
@@ -196,11 +198,9 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   k.sigma = params->sigma;
   k.eps = params->eps_phi;
   k.pv0 = params->p_v0;
-  k.divx = make_fastdiv((unsigned)k.nx);
-  k.divy = make_fastdiv((unsigned)k.ny);
-  for (int i = 0; i < 27; ++i) {
-    k.off[i] = CX(i) + k.nx * (CY(i) + k.ny * CZ(i));
-    k.dofs[i] = (long long)i * k.Np - k.off[i];
+  {
+    const int identity[3] = {0, 1, 2};
+    set_layout(k, identity);
   }
   k.variant = (int)bc_variant;
   k.om3_fb = params->om3_fallback;
@@ -229,7 +229,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   std::memset(&d, 0, sizeof(d));
   const size_t n4 = (size_t)((N + 3) / 4 * 4);
   cudaError_t e = cudaSuccess;
-  const size_t pdf_bytes = (size_t)c->q * (size_t)k.Np * c->ops.elem_size;
+  const size_t pdf_bytes = pdf_buffer_bytes(c->ops, c->q, k.Np);
   const size_t rs = c->ops.real_size;
 #define ALLOC(ptr, bytes)                                 \
   if (e == cudaSuccess) e = dalloc(c, &(ptr), (bytes));
@@ -295,23 +295,27 @@ fslbm_status fslbm_memory_estimate(const fslbm_domain* domain, fslbm_lattice lat
                                    int with_velocity, size_t* bytes) {
   if (!domain || !bytes || domain->nx < 1 || domain->ny < 1 || domain->nz < 1) return FSLBM_EINVAL;
   if (lattice != FSLBM_D3Q19 && lattice != FSLBM_D3Q27) return FSLBM_EINVAL;
-  if (precision < FSLBM_FP64 || precision > FSLBM_BF16S) return FSLBM_EINVAL;
+  if (precision < FSLBM_FP64 || precision > FSLBM_FP16SMC) return FSLBM_EINVAL;
   const double Nd = (double)domain->nx * domain->ny * domain->nz;
   if (Nd > 2147483647.0) return FSLBM_EINVAL;
   const size_t N = (size_t)Nd;
   const size_t Np = (N + 63) / 64 * 64;
-  const size_t elem = precision == FSLBM_FP64 ? 8 : precision == FSLBM_FP32 ? 4 : 2;
+  const size_t elem = precision == FSLBM_FP64 ? 8
+                      : (precision == FSLBM_FP32 || precision == FSLBM_FP32MC) ? 4
+                                                                               : 2;
+  const size_t rest = (precision == FSLBM_FP32MC || precision == FSLBM_FP16SMC) ? 8 : 0;
   const size_t rs = precision == FSLBM_FP64 ? 8 : 4;
   const size_t n4 = (N + 3) / 4 * 4;
   const size_t ntiles =
       (size_t)((domain->nx + 7) / 8) * ((domain->ny + 7) / 8) * ((domain->nz + 7) / 8);
   const size_t nseg = (N + kSegCells - 1) / kSegCells;
-  size_t b = 2 * (size_t)lattice * Np * elem;            // PDFs, two buffers
+  size_t b = 2 * ((size_t)lattice * Np * elem + Np * rest);  // PDFs, two buffers
   b += 6 * n4 + (N + 31) / 32 * 32;                      // cls, mark, conv, cfin, claim, rcv; flags
   b += N * (4 + 8 + 8 + 4 + 8 + 4 + 4 + 4);              // wallmask phi mass bid share band[2] newlist
   b += N * (7 * rs + 4 * 8);                             // nhat rhog mom m_next phi_next rho_band
   b += 3 * ntiles * 4 + 2 * nseg * 4 + 4096;             // tiles, segments, counters, partials
-  b += N * (1 + 8 + 8) + (with_velocity ? 24 * N : 0);   // fslbm_init staging (peak)
+  b += 2 * (N * (1 + 8 + 8) + (with_velocity ? 24 * N : 0));  // fslbm_init staging in the
+                                                           // caller's and the storage order
   *bytes = b;
   return FSLBM_OK;
 }
@@ -330,6 +334,63 @@ void fslbm_destroy(fslbm_ctx* c) {
   delete c;
 }
 
+namespace {
+
+// Storage order for a domain's initial flags (caller order, on the device):
+// the contiguous axis with the fewest liquid-holding 32-cell groups, i.e.
+// the fullest warps of the bulk sweep, the other two axes in the caller's
+// order.  x stays contiguous unless another axis needs at most 95 % of its
+// groups.
+cudaError_t choose_layout(fslbm_ctx* c, const uint8_t* raw_ext, int ax[3]) {
+  ax[0] = 0;
+  ax[1] = 1;
+  ax[2] = 2;
+  unsigned long long* cnt = nullptr;
+  cudaError_t e = dalloc(c, &cnt, 3 * sizeof(unsigned long long));
+  unsigned long long h[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), c->stream);
+  const int grid = (c->kp.N + kBlock - 1) / kBlock;
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+    KParams k = c->kp;
+    const int order[3] = {a, a == 0 ? 1 : 0, a == 2 ? 1 : 2};
+    set_layout(k, order);
+    k_layout_census<<<grid, kBlock, 0, c->stream>>>(raw_ext, k, cnt + a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, cnt);
+  if (e != cudaSuccess) return e;
+  int best = 0;
+  for (int a = 1; a < 3; ++a)
+    if ((double)h[a] <= 0.95 * (double)h[0] && h[a] < h[best]) best = a;
+  ax[0] = best;
+  ax[1] = best == 0 ? 1 : 0;
+  ax[2] = best == 2 ? 1 : 2;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+fslbm_status fslbm_set_axis_order(fslbm_ctx* c, const int* order) {
+  if (!c) return FSLBM_EINVAL;
+  if (!order) {
+    c->req_axis[0] = c->req_axis[1] = c->req_axis[2] = -1;
+    return FSLBM_OK;
+  }
+  const bool ok = order[0] >= 0 && order[0] < 3 && order[1] >= 0 && order[1] < 3 && order[2] >= 0 &&
+                  order[2] < 3 && order[0] != order[1] && order[0] != order[2] && order[1] != order[2];
+  if (!ok) return fail(c, FSLBM_EINVAL, "axis order must be a permutation of 0, 1, 2");
+  for (int a = 0; a < 3; ++a) c->req_axis[a] = order[a];
+  return FSLBM_OK;
+}
+
+fslbm_status fslbm_get_axis_order(const fslbm_ctx* c, int* order) {
+  if (!c || !order) return FSLBM_EINVAL;
+  for (int a = 0; a < 3; ++a) order[a] = c->kp.ax[a];
+  return FSLBM_OK;
+}
+
 fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
                         const double* velocity, const double* density) {
   if (!c) return FSLBM_EINVAL;
@@ -338,27 +399,59 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   // flag values and the closed interface layer are checked on the device
   // (k_init_check) once the flags are uploaded
   cudaStream_t st = c->stream;
-  uint8_t* raw = nullptr;
+  uint8_t *raw = nullptr, *raw_ext = nullptr;
   double *dfill = nullptr, *dvel = nullptr, *dden = nullptr;
+  double *fill_ext = nullptr, *vel_ext = nullptr, *den_ext = nullptr;
   int* bad = nullptr;
-  cudaError_t e = dalloc(c, &raw, N);
-  if (e == cudaSuccess) e = dalloc(c, &dfill, N * sizeof(double));
-  if (e == cudaSuccess && velocity) e = dalloc(c, &dvel, 3 * N * sizeof(double));
-  if (e == cudaSuccess && density) e = dalloc(c, &dden, N * sizeof(double));
+  cudaError_t e = dalloc(c, &raw_ext, N);
+  if (e == cudaSuccess) e = dalloc(c, &fill_ext, N * sizeof(double));
+  if (e == cudaSuccess && velocity) e = dalloc(c, &vel_ext, 3 * N * sizeof(double));
+  if (e == cudaSuccess && density) e = dalloc(c, &den_ext, N * sizeof(double));
   if (e == cudaSuccess) e = dalloc(c, &bad, sizeof(int));
   auto cleanup = [&]() {
-    dfree(c, raw);
-    dfree(c, dfill);
-    dfree(c, dvel);
-    dfree(c, dden);
+    if (raw != raw_ext) dfree(c, raw);
+    if (dfill != fill_ext) dfree(c, dfill);
+    if (dvel != vel_ext) dfree(c, dvel);
+    if (dden != den_ext) dfree(c, dden);
+    dfree(c, raw_ext);
+    dfree(c, fill_ext);
+    dfree(c, vel_ext);
+    dfree(c, den_ext);
     dfree(c, bad);
   };
-  if (e == cudaSuccess) e = cudaMemcpyAsync(raw, flags, N, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dfill, fill, N * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw_ext, flags, N, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(fill_ext, fill, N * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && velocity)
-    e = cudaMemcpyAsync(dvel, velocity, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(vel_ext, velocity, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && density)
-    e = cudaMemcpyAsync(dden, density, N * sizeof(double), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(den_ext, density, N * sizeof(double), cudaMemcpyHostToDevice, st);
+  // storage order: the requested one, else the one whose bulk warps are
+  // fullest for these flags; the previous one is restored if init fails
+  const KParams kp_prev = c->kp;
+  int ax[3] = {c->req_axis[0], c->req_axis[1], c->req_axis[2]};
+  if (e == cudaSuccess && ax[0] < 0) e = choose_layout(c, raw_ext, ax);
+  if (e == cudaSuccess) set_layout(c->kp, ax);
+  raw = raw_ext;
+  dfill = fill_ext;
+  dvel = vel_ext;
+  dden = den_ext;
+  if (e == cudaSuccess && !is_identity_layout(c->kp)) {
+    // staging copies in the storage order
+    const int grid = (c->kp.N + kBlock - 1) / kBlock;
+    raw = nullptr;
+    dfill = dvel = dden = nullptr;
+    e = dalloc(c, &raw, N);
+    if (e == cudaSuccess) e = dalloc(c, &dfill, N * sizeof(double));
+    if (e == cudaSuccess && velocity) e = dalloc(c, &dvel, 3 * N * sizeof(double));
+    if (e == cudaSuccess && density) e = dalloc(c, &dden, N * sizeof(double));
+    if (e == cudaSuccess) {
+      k_to_storage<uint8_t><<<grid, kBlock, 0, st>>>(raw_ext, raw, c->kp, 1);
+      k_to_storage<double><<<grid, kBlock, 0, st>>>(fill_ext, dfill, c->kp, 1);
+      if (velocity) k_to_storage<double><<<grid, kBlock, 0, st>>>(vel_ext, dvel, c->kp, 3);
+      if (density) k_to_storage<double><<<grid, kBlock, 0, st>>>(den_ext, dden, c->kp, 1);
+      e = cudaGetLastError();
+    }
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
   int hbad = 0;
   if (e == cudaSuccess) {
@@ -369,10 +462,12 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cleanup();
+    c->kp = kp_prev;
     return cuda_fail(c, e, "fslbm_init upload");
   }
   if (hbad) {
     cleanup();
+    c->kp = kp_prev;
     return fail(c, FSLBM_EINVAL,
                 (hbad & 1) ? "flag value > 3"
                            : "a liquid cell touches a gas cell (interface layer not closed)");
@@ -400,9 +495,9 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
       k_cc_init<<<gcells, kBlock, 0, st>>>(raw, c->kp.N, lab);
       c->ops.cc_union(raw, c->kp, lab, st);
       k_cc_compress<<<gcells, kBlock, 0, st>>>(c->kp.N, lab);
-      k_cc_count<<<nchunks, kBlock, 0, st>>>(c->kp.N, lab, cnt);
+      k_cc_count<<<nchunks, kBlock, 0, st>>>(c->kp, lab, cnt);
       k_cc_scan<<<1, 1024, 0, st>>>(nchunks, cnt, off);
-      k_cc_number<<<nchunks, 32, 0, st>>>(c->kp.N, lab, off, root_id);
+      k_cc_number<<<nchunks, 32, 0, st>>>(c->kp, lab, off, root_id);
       c->ops.cc_assign(raw, c->kp, lab, root_id, d.bid, st);
       e = cudaGetLastError();
     }
@@ -432,7 +527,7 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   }
   // clear both PDF buffers: gas and obstacle slots hold no PDFs of their
   // own (obstacle slots receive reflected copies from their neighbours)
-  const size_t pdf_bytes = (size_t)c->q * (size_t)c->kp.Np * c->ops.elem_size;
+  const size_t pdf_bytes = pdf_buffer_bytes(c->ops, c->q, c->kp.Np);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.pdf[0], 0, pdf_bytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.pdf[1], 0, pdf_bytes, st);
   if (e == cudaSuccess) {
@@ -557,12 +652,35 @@ fslbm_status fslbm_read_fields(fslbm_ctx* c, double* pdf, double* fill, uint8_t*
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     dfree(c, tmp);
   }
-  if (e == cudaSuccess && fill)
-    e = cudaMemcpyAsync(fill, c->d.phi, N * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && mass)
-    e = cudaMemcpyAsync(mass, c->d.mass, N * sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, c->d.flags, N, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (is_identity_layout(c->kp)) {
+    if (e == cudaSuccess && fill)
+      e = cudaMemcpyAsync(fill, c->d.phi, N * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && mass)
+      e = cudaMemcpyAsync(mass, c->d.mass, N * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, c->d.flags, N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  } else if (e == cudaSuccess && (fill || mass || flags)) {
+    // the fields in the caller's cell order, through one staging array
+    double* tmp = nullptr;
+    e = dalloc(c, &tmp, N * sizeof(double));
+    const int grid = (c->kp.N + kBlock - 1) / kBlock;
+    auto out = [&](const double* src, double* host) {
+      if (e != cudaSuccess || !host) return;
+      k_to_caller<double><<<grid, kBlock, 0, st>>>(src, tmp, c->kp);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    };
+    out(c->d.phi, fill);
+    out(c->d.mass, mass);
+    if (e == cudaSuccess && flags) {
+      k_to_caller<uint8_t><<<grid, kBlock, 0, st>>>(c->d.flags, (uint8_t*)tmp, c->kp);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(flags, tmp, N, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    dfree(c, tmp);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_read_fields");
   if (flags)
     for (size_t i = 0; i < N; ++i) flags[i] &= F_TYPE;
@@ -635,9 +753,12 @@ fslbm_status fslbm_work_counts(fslbm_ctx* c, int64_t* interface_cells, int64_t* 
 
 // ------------------------------------------------------------ checkpoints
 namespace {
+// The arrays are saved in the context's storage order, which the header
+// records; a checkpoint loads only into a context with the same order.
 struct CkptHeader {
   char magic[8];
   int nx, ny, nz, q, precision, nb;
+  int ax[3], reserved;
   int64_t step;
   int64_t pdf_bytes;
 };
@@ -648,7 +769,7 @@ fslbm_status fslbm_save(fslbm_ctx* c, void* buf, size_t* size) {
   if (!c->initialized) return fail(c, FSLBM_ESTATE, "save before init");
   const size_t N = (size_t)c->kp.N;
   const size_t nb = (size_t)c->d.nb;
-  const size_t pdf_bytes = (size_t)c->q * (size_t)c->kp.Np * c->ops.elem_size;
+  const size_t pdf_bytes = pdf_buffer_bytes(c->ops, c->q, c->kp.Np);
   const size_t need = sizeof(CkptHeader) + pdf_bytes + N + 2 * N * sizeof(double) +
                       N * sizeof(int) + nb * (3 * sizeof(double) + sizeof(long long));
   if (!buf) {
@@ -658,13 +779,14 @@ fslbm_status fslbm_save(fslbm_ctx* c, void* buf, size_t* size) {
   if (*size < need) return fail(c, FSLBM_EINVAL, "checkpoint buffer too small");
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
-  std::memcpy(h.magic, "FSLBMCK1", 8);
+  std::memcpy(h.magic, "FSLBMCK2", 8);
   h.nx = c->kp.nx;
   h.ny = c->kp.ny;
   h.nz = c->kp.nz;
   h.q = c->q;
   h.precision = c->prm.precision;
   h.nb = (int)nb;
+  for (int a = 0; a < 3; ++a) h.ax[a] = c->kp.ax[a];
   h.step = c->step;
   h.pdf_bytes = (int64_t)pdf_bytes;
   char* p = (char*)buf;
@@ -696,10 +818,11 @@ fslbm_status fslbm_load(fslbm_ctx* c, const void* buf, size_t size) {
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
   const size_t N = (size_t)c->kp.N;
-  const size_t pdf_bytes = (size_t)c->q * (size_t)c->kp.Np * c->ops.elem_size;
-  if (std::memcmp(h.magic, "FSLBMCK1", 8) != 0 || h.nx != c->kp.nx || h.ny != c->kp.ny ||
+  const size_t pdf_bytes = pdf_buffer_bytes(c->ops, c->q, c->kp.Np);
+  if (std::memcmp(h.magic, "FSLBMCK2", 8) != 0 || h.nx != c->kp.nx || h.ny != c->kp.ny ||
       h.nz != c->kp.nz || h.q != c->q || h.precision != c->prm.precision || h.nb != c->d.nb ||
-      h.pdf_bytes != (int64_t)pdf_bytes)
+      h.pdf_bytes != (int64_t)pdf_bytes || h.ax[0] != c->kp.ax[0] || h.ax[1] != c->kp.ax[1] ||
+      h.ax[2] != c->kp.ax[2])
     return fail(c, FSLBM_EINVAL, "checkpoint does not match this context");
   const size_t nb = (size_t)h.nb;
   const size_t need = sizeof(CkptHeader) + pdf_bytes + N + 2 * N * sizeof(double) +

@@ -33,21 +33,29 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
   T* __restrict__ B = (T*)d.pdf[parity ^ 1];
   const long long Np = p.Np;
   R f[Q];
+  // the mass-conserving formats hold the rest PDF in an FP64 slice
+  constexpr int i0 = S::kExactRest ? 1 : 0;
   if (!general) {
     const T* Ac = A + c;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(Ac[p.dofs[i]], i);
+    for (int i = i0; i < Q; ++i) f[i] = load_w<S, Q>(Ac[p.dofs[i]], i);
   } else {
     int x, y, z;
     decode(p, c, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(A[pull_index_general<Q>(p, c, x, y, z, i)], i);
+    for (int i = i0; i < Q; ++i) f[i] = load_w<S, Q>(A[pull_index_general<Q>(p, c, x, y, z, i)], i);
+  }
+  double s_in = 0.0;
+  if constexpr (S::kExactRest) {
+    // the received stored values, summed exactly
+    s_in = rest_slice<Q, S>(A, Np)[c];
+    f[0] = (R)s_in;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s_in += (double)f[i];
   }
   bool bad = false;
   collide_any<Q, S, COLL>(f, p, bad);
-  T* Bc = B + c;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) Bc[(long long)i * Np] = store_w<S, Q>(f[i], i);
+  store_cell<Q, S>(B, Np, c, f, s_in);
   if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], general, f);
   if (bad) d.err[0] = 1;
 }
@@ -85,7 +93,11 @@ __device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int 
     if (grp && t == T_GAS) {
       T* __restrict__ B = (T*)d.pdf[parity ^ 1];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
+      for (int i = S::kExactRest ? 1 : 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
+    }
+    if constexpr (S::kExactRest) {
+      // the FP64 rest slice: 4 cells per 32-byte sector
+      if (((lm >> (lane & ~3)) & 0xfu) && t == T_GAS) rest_slice<Q, S>(d.pdf[parity ^ 1], p.Np)[c] = 0.0;
     }
   }
 }

@@ -18,11 +18,28 @@ __device__ __forceinline__ int wrapc(int X, int n, int per) {
   if (X < 0) X += n;
   return X;
 }
+__device__ __forceinline__ int sel3(int k, int a0, int a1, int a2) {
+  return k == 0 ? a0 : (k == 1 ? a1 : a2);
+}
+// caller coordinates (x, y, z) of the cell with storage index c
 __device__ __forceinline__ void decode(const KParams& p, int c, int& x, int& y, int& z) {
-  const int t = (int)p.divx.div((unsigned)c);
-  x = c - t * p.nx;
-  z = (int)p.divy.div((unsigned)t);
-  y = t - z * p.ny;
+  const int t = (int)p.div0.div((unsigned)c);
+  const int a0 = c - t * p.m0;
+  const int a2 = (int)p.div1.div((unsigned)t);
+  const int a1 = t - a2 * p.m1;
+  x = sel3(p.inv[0], a0, a1, a2);
+  y = sel3(p.inv[1], a0, a1, a2);
+  z = sel3(p.inv[2], a0, a1, a2);
+}
+// storage index of the cell at caller coordinates (X, Y, Z) inside the domain
+__device__ __forceinline__ int cidx(const KParams& p, int X, int Y, int Z) {
+  return X * p.sx + Y * p.sy + Z * p.sz;
+}
+// the caller's index x + nx (y + ny z) of the cell with storage index c
+__device__ __forceinline__ int ext_index(const KParams& p, int c) {
+  int x, y, z;
+  decode(p, c, x, y, z);
+  return x + p.nx * (y + p.ny * z);
 }
 // neighbour of (x,y,z) at offset (dx,dy,dz); -1 outside a non-periodic face
 __device__ __forceinline__ int nbr(const KParams& p, int x, int y, int z, int dx, int dy,
@@ -31,7 +48,7 @@ __device__ __forceinline__ int nbr(const KParams& p, int x, int y, int z, int dx
   int Y = wrapc(y + dy, p.ny, p.per[1]);
   int Z = wrapc(z + dz, p.nz, p.per[2]);
   if (X < 0 || Y < 0 || Z < 0) return -1;
-  return X + p.nx * (Y + p.ny * Z);
+  return cidx(p, X, Y, Z);
 }
 __device__ __forceinline__ int ntype(const uint8_t* flags, int n) {
   return n < 0 ? T_OBST : (flags[n] & F_TYPE);
@@ -268,6 +285,52 @@ __device__ __forceinline__ typename S::T store_w(typename S::Real v, int i) {
     return S::store(v, W<Q, typename S::Real>(i));
 }
 
+// ------------------------------------------- mass-conserving formats
+// The FP64 rest slice that follows the q slices of a PDF buffer.
+template <int Q, class S>
+__device__ __forceinline__ double* rest_slice(const void* P, long long Np) {
+  return (double*)((typename S::T*)P + (long long)Q * Np);
+}
+template <class S>
+__device__ __forceinline__ double snap_rest(double d0) {
+  return snap_grid(d0, S::kGrid, 1.0 / S::kGrid);
+}
+
+// Stores the post-collision PDFs f (working representation) of storage
+// cell c into buffer B.  For the mass-conserving formats s_in is the FP64
+// sum of the values the collision received: the rest deviation becomes
+// s_in minus the sum of the stored moving values (exact when the inputs
+// were stored values, as for liquid cells; rounded to the grid otherwise).
+template <int Q, class S>
+__device__ __forceinline__ void store_cell(typename S::T* B, long long Np, long long c,
+                                           const typename S::Real* f, double s_in) {
+  if constexpr (S::kExactRest) {
+    double s_out = 0.0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const typename S::T v = S::stored(f[i]);
+      B[(long long)i * Np + c] = v;
+      s_out += (double)S::loadd(v);
+    }
+    rest_slice<Q, S>(B, Np)[c] = snap_rest<S>(s_in - s_out);
+  } else {
+    (void)s_in;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
+  }
+}
+
+// PDF i of storage cell c of buffer P in the working representation (the
+// rest PDF of the mass-conserving formats from its FP64 slice).
+template <int Q, class S>
+__device__ __forceinline__ typename S::Real load_own(const typename S::T* P, long long Np, long long c,
+                                                     int i) {
+  if constexpr (S::kExactRest) {
+    if (i == 0) return (typename S::Real)rest_slice<Q, S>(P, Np)[c];
+  }
+  return load_w<S, Q>(P[(long long)i * Np + c], i);
+}
+
 // rho and u of a cell from its post-collision PDFs: rho u = sum c f* - F/2.
 // With deviations, rho = 1 + sum d is summed in FP64 from the stored values,
 // so that it equals the cell's mass as the PDFs hold it.
@@ -278,14 +341,15 @@ __device__ __forceinline__ void post_moments(const typename S::T* P, long long N
   using R = typename S::Real;
   R f[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) f[i] = load_w<S, Q>(P[(long long)i * Np + c], i);
+  for (int i = 0; i < Q; ++i) f[i] = load_own<Q, S>(P, Np, c, i);
   R r, jx, jy, jz;
   sums<Q, R>(f, r, jx, jy, jz);
   R rr = r;
   if constexpr (S::kDev) {
     double sd = 0.0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) sd += (double)f[i];
+    for (int i = 0; i < Q; ++i)
+      sd += (S::kExactRest && i == 0) ? rest_slice<Q, S>(P, Np)[c] : (double)f[i];
     rho = 1.0 + sd;
     rr = R(rho);
   } else {
@@ -317,7 +381,7 @@ __device__ __forceinline__ long long pull_index_general(const KParams& p, int c,
     if (p.per[2]) Z = Z < 0 ? Z + p.nz : Z - p.nz;
     else out = true;
   }
-  return out ? (long long)OPP(i) * p.Np + c : (long long)i * p.Np + (X + p.nx * (Y + p.ny * Z));
+  return out ? (long long)OPP(i) * p.Np + c : (long long)i * p.Np + cidx(p, X, Y, Z);
 }
 
 // Reflected copies of a fluid cell's post-collision PDFs (working

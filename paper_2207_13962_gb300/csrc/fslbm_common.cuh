@@ -94,6 +94,7 @@ struct StoreF64 {
   using Real = double;
   static constexpr int code = 0;
   static constexpr bool kDev = false;
+  static constexpr bool kExactRest = false;
   __device__ static __forceinline__ Real load(T v, Real) { return v; }
   __device__ static __forceinline__ T store(Real f, Real) { return f; }
 };
@@ -102,6 +103,7 @@ struct StoreF32 {
   using Real = float;
   static constexpr int code = 1;
   static constexpr bool kDev = true;
+  static constexpr bool kExactRest = false;
   __device__ static __forceinline__ float loadd(T v) { return v; }
   __device__ static __forceinline__ T stored(float d) { return d; }
   __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
@@ -112,6 +114,7 @@ struct StoreF16S {
   using Real = float;
   static constexpr int code = 2;
   static constexpr bool kDev = true;
+  static constexpr bool kExactRest = false;
   __device__ static __forceinline__ float loadd(T v) { return __half2float(v) * 0x1p-15f; }
   __device__ static __forceinline__ T stored(float d) { return __float2half_rn(d * 0x1p15f); }
   __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
@@ -122,8 +125,52 @@ struct StoreBF16S {
   using Real = float;
   static constexpr int code = 3;
   static constexpr bool kDev = true;
+  static constexpr bool kExactRest = false;
   __device__ static __forceinline__ float loadd(T v) { return __bfloat162float(v); }
   __device__ static __forceinline__ T stored(float d) { return __float2bfloat16_rn(d); }
+  __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
+};
+
+// Mass-conserving variants of the FP32 and FP16 deviation formats.  The
+// q - 1 moving deviations are stored as in the base format but lie on the
+// grid of multiples of 2^-kGrid (FP32 values are rounded to it; FP16 values
+// d 2^15 are multiples of the smallest subnormal 2^-24, so d is a multiple
+// of 2^-39 already), and the rest deviation d_0 is stored in FP64, on the
+// same grid, in a slice of its own after the q slices of the buffer.  A
+// collision stores d_0 = (sum of the stored values it received) - (sum of
+// the q - 1 moving values it stores).  Every term is a multiple of 2^-kGrid
+// far below 2^53 of them, so both sums and the difference are exact in
+// FP64: a liquid cell's stored sum (its density) is exactly the one it
+// received, streaming and bounce-back move stored values unchanged, and
+// the total mass of the liquid does not drift.
+__device__ __forceinline__ float snap_grid(float d, float scale, float inv) {
+  return rintf(d * scale) * inv;  // both products are exact (powers of 2)
+}
+__device__ __forceinline__ double snap_grid(double d, double scale, double inv) {
+  return rint(d * scale) * inv;
+}
+struct StoreF32MC {
+  using T = float;
+  using Real = float;
+  static constexpr int code = 4;
+  static constexpr bool kDev = true;
+  static constexpr bool kExactRest = true;
+  static constexpr double kGrid = 0x1p44;  // grid 2^-44
+  __device__ static __forceinline__ float loadd(T v) { return v; }
+  __device__ static __forceinline__ T stored(float d) { return snap_grid(d, 0x1p44f, 0x1p-44f); }
+  __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
+  __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
+};
+struct StoreF16SMC {
+  using T = __half;
+  using Real = float;
+  static constexpr int code = 5;
+  static constexpr bool kDev = true;
+  static constexpr bool kExactRest = true;
+  static constexpr double kGrid = 0x1p39;  // grid 2^-39
+  __device__ static __forceinline__ float loadd(T v) { return __half2float(v) * 0x1p-15f; }
+  __device__ static __forceinline__ T stored(float d) { return __float2half_rn(d * 0x1p15f); }
   __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
   __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
 };
@@ -167,9 +214,20 @@ constexpr int kSegCells = FSLBM_SEG_CELLS;
 static_assert(kSegCells == 8 || kSegCells == 16 || kSegCells == 32, "segment size");
 
 // ----------------------------------------------------------- parameters
+// Storage order of the cells.  The caller's coordinates (x, y, z) and cell
+// index x + nx (y + ny z) are fixed; inside the library any axis may be the
+// contiguous one.  ax[k] is the caller's axis at storage position k (k = 0
+// contiguous), so a cell's storage index is c = a0 + m0 (a1 + m1 a2), a_k
+// its coordinate along axis ax[k] and m_k that axis' size; sx, sy, sz are
+// the strides of x, y, z in c and inv[a] the storage position of axis a.
+// Direction labels, their vectors and all arithmetic stay in the caller's
+// axes: only index computations see the storage order.
 struct KParams {
-  FastDiv divx, divy;
-  int off[27];         // cell-index offset of direction i: cx + nx (cy + ny cz)
+  FastDiv div0, div1;  // division by m0 and m1 (decoding a storage index)
+  int ax[3], inv[3];
+  int m0, m1;
+  int sx, sy, sz;
+  int off[27];         // storage-index offset of direction i: c_i . (sx, sy, sz)
   long long dofs[27];  // i * Np - off[i]: pull source of interior cells
   int nx, ny, nz;
   int per[3];
@@ -180,6 +238,33 @@ struct KParams {
   double sigma, eps, pv0;
   int variant, om3_fb, bubble_model, collision;
 };
+
+// Fills the storage-order fields of k (nx, ny, nz and Np already set) for
+// the axis order ax (a permutation of 0, 1, 2; ax[0] contiguous).
+inline void set_layout(KParams& k, const int ax[3]) {
+  const int n[3] = {k.nx, k.ny, k.nz};
+  int s[3];
+  for (int pos = 0; pos < 3; ++pos) {
+    k.ax[pos] = ax[pos];
+    k.inv[ax[pos]] = pos;
+  }
+  k.m0 = n[ax[0]];
+  k.m1 = n[ax[1]];
+  s[ax[0]] = 1;
+  s[ax[1]] = k.m0;
+  s[ax[2]] = k.m0 * k.m1;
+  k.sx = s[0];
+  k.sy = s[1];
+  k.sz = s[2];
+  k.div0 = make_fastdiv((unsigned)k.m0);
+  k.div1 = make_fastdiv((unsigned)k.m1);
+  for (int i = 0; i < 27; ++i) {
+    k.off[i] = CX(i) * k.sx + CY(i) * k.sy + CZ(i) * k.sz;
+    k.dofs[i] = (long long)i * k.Np - k.off[i];
+  }
+}
+
+inline bool is_identity_layout(const KParams& k) { return k.ax[0] == 0 && k.ax[1] == 1 && k.ax[2] == 2; }
 
 // Device pointers of one domain.
 struct DPtrs {

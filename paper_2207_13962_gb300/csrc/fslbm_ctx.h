@@ -25,6 +25,7 @@ struct fslbm_ctx {
   int q = 19, collision = 1, variant = 3;
   fslbm_params prm;
   fslbm::KParams kp;
+  int req_axis[3] = {-1, -1, -1};  // requested storage order, -1: chosen at init
   fslbm::DPtrs d;
   fslbm::Ops ops;
   cudaStream_t stream = nullptr;

@@ -11,7 +11,7 @@ namespace fslbm {
 template <int Q, class S>
 struct Engine {
   // the FP32 and 16-bit engines stream the bulk sweep through TMA copies
-  static constexpr bool kTmaBulk = S::kDev && FSLBM_BULK_TMA != 0;
+  static constexpr bool kTmaBulk = S::kDev && !S::kExactRest && FSLBM_BULK_TMA != 0;
   // persistent bulk blocks per SM the sweep is compiled for
   static constexpr int bulk_blocks_per_sm() {
     return sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2;
@@ -146,6 +146,7 @@ struct Engine {
     o.pdf_out = &pdf_out;
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::Real);
+    o.rest_size = S::kExactRest ? sizeof(double) : 0;
     if constexpr (kTmaBulk) {
       o.bulk_fn[0] = (const void*)&k_bulk_tma<Q, S, 0>;
       o.bulk_fn[1] = (const void*)&k_bulk_tma<Q, S, 1>;

@@ -39,6 +39,7 @@ struct Ops {
   void (*pdf_out)(const DPtrs&, const KParams&, int parity, double* out, cudaStream_t);
   size_t elem_size;
   size_t real_size;
+  size_t rest_size;        // bytes per cell of the FP64 rest slice (0: none)
   const void* bulk_fn[2];  // the bulk sweep kernels (SRT, TRT): graph nodes of
                            // every other kernel get the higher priority
   int bulk_blocks_per_sm;  // resident blocks per SM of the persistent bulk sweep
@@ -54,5 +55,13 @@ Ops ops_f64(int q);
 Ops ops_f32(int q);
 Ops ops_f16s(int q);
 Ops ops_bf16s(int q);
+Ops ops_f32mc(int q);
+Ops ops_f16smc(int q);
+
+// Bytes of one PDF buffer: q slices of Np stored values, plus the FP64 rest
+// slice of the mass-conserving formats.
+inline size_t pdf_buffer_bytes(const Ops& o, int q, long long Np) {
+  return (size_t)q * (size_t)Np * o.elem_size + (size_t)Np * o.rest_size;
+}
 
 }  // namespace fslbm

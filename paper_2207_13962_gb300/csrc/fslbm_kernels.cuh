@@ -102,11 +102,10 @@ __global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __re
 #pragma unroll
     for (int i = 0; i < Q; ++i) fe[i] = feq_i<Q, R>(i, R(r), ux, uy, uz);
   }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    P[(long long)i * p.Np + c] = store_w<S, Q>(fe[i], i);
-    P2[(long long)i * p.Np + c] = store_w<S, Q>(fe[i], i);
-  }
+  // the mass-conserving formats store the density deviation r - 1 exactly
+  // (to their grid): the rest PDF takes up the rounding of the others
+  store_cell<Q, S>(P, p.Np, c, fe, r - 1.0);
+  store_cell<Q, S>(P2, p.Np, c, fe, r - 1.0);
   if (wm) {
     write_reflected<Q, S>(d, p, P, c, wm, (fl & F_WRAP) != 0, fe);
     write_reflected<Q, S>(d, p, P2, c, wm, (fl & F_WRAP) != 0, fe);
@@ -125,11 +124,12 @@ static __global__ void k_compact_full(const uint8_t* __restrict__ flags, int N, 
 // -------------------------------------------------------- bubble labels
 // Connected gas regions (lattice neighbourhood, periodic wrap) at init, on
 // the device.  Union-find with lock-free hooking: every gas cell starts as
-// its own root; a union hooks the larger of two roots under the smaller one
-// with compare-and-swap (a root is re-parented only while it is still a
-// root), so labels only decrease and every root ends as the lowest cell
-// index of its component.  Bubbles are then numbered in the order of their
-// roots, i.e. of their lowest cell index.
+// its own root; a union hooks the root with the larger caller index
+// x + nx (y + ny z) under the other with compare-and-swap (a root is
+// re-parented only while it is still a root), so every root ends as the
+// cell of its component with the lowest caller index, whatever the storage
+// order.  Bubbles are then numbered in the order of their roots' caller
+// indices, i.e. of their lowest cell index.
 __device__ __forceinline__ int cc_find(const int* lab, int x) {
   int p = lab[x];
   while (p != x) {
@@ -152,10 +152,10 @@ __global__ void k_cc_union(const uint8_t* __restrict__ raw, KParams p, int* lab)
   decode(p, c, x, y, z);
   for (int i = 1; i < Q; ++i) {
     const int n = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
-    if (n < 0 || n >= c || raw[n] != T_GAS) continue;  // each pair once
+    if (n < 0 || n >= c || raw[n] != T_GAS) continue;  // each pair once (storage order)
     int a = cc_find(lab, c), b = cc_find(lab, n);
     while (a != b) {
-      if (a > b) {
+      if (ext_index(p, a) > ext_index(p, b)) {
         const int t = a;
         a = b;
         b = t;
@@ -173,16 +173,27 @@ static __global__ void k_cc_compress(int N, int* lab) {
   if (c < N && lab[c] >= 0) lab[c] = cc_find(lab, c);
 }
 
-// Roots per block of kCcChunk cells (pass 1 of the numbering).
+// Storage index of the cell with caller index e.
+__device__ __forceinline__ int storage_of_ext(const KParams& p, int e) {
+  const int x = e % p.nx, t = e / p.nx;
+  return cidx(p, x, t % p.ny, t / p.ny);
+}
+
+// Roots per block of kCcChunk cells, counted in the caller's cell order
+// (pass 1 of the numbering).
 constexpr int kCcChunk = 1024;
-static __global__ void k_cc_count(int N, const int* __restrict__ lab, int* block_roots) {
+static __global__ void k_cc_count(KParams p, const int* __restrict__ lab, int* block_roots) {
   __shared__ int cnt;
+  const int N = p.N;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   int mine = 0;
   for (int k = threadIdx.x; k < kCcChunk; k += blockDim.x) {
-    const long long c = (long long)blockIdx.x * kCcChunk + k;
-    if (c < N && lab[c] == (int)c) ++mine;
+    const long long e = (long long)blockIdx.x * kCcChunk + k;
+    if (e < N) {
+      const int c = storage_of_ext(p, (int)e);
+      if (lab[c] == c) ++mine;
+    }
   }
   atomicAdd(&cnt, mine);
   __syncthreads();
@@ -194,11 +205,12 @@ static __global__ void k_cc_scan(int nblocks, const int* __restrict__ block_root
   block_prefix(nblocks, off, [&](int k) { return block_roots[k]; });
 }
 
-// Bubble id of every root in index order (pass 2): warps walk their block's
-// chunk in order, so ranks within the chunk follow the cell index.
-static __global__ void k_cc_number(int N, const int* __restrict__ lab, const int* __restrict__ off,
+// Bubble id of every root in the caller's index order (pass 2): warps walk
+// their block's chunk in order, so ranks within the chunk follow the index.
+static __global__ void k_cc_number(KParams p, const int* __restrict__ lab, const int* __restrict__ off,
                                    int* root_id) {
   __shared__ int base;
+  const int N = p.N;
   if (threadIdx.x == 0) base = off[blockIdx.x];
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -206,8 +218,9 @@ static __global__ void k_cc_number(int N, const int* __restrict__ lab, const int
   if (threadIdx.x < 32) {
     int b = base;
     for (int k = 0; k < kCcChunk; k += 32) {
-      const long long c = (long long)blockIdx.x * kCcChunk + k + lane;
-      const bool root = c < N && lab[c] == (int)c;
+      const long long e = (long long)blockIdx.x * kCcChunk + k + lane;
+      const int c = e < N ? storage_of_ext(p, (int)e) : -1;
+      const bool root = c >= 0 && lab[c] == c;
       const unsigned m = __ballot_sync(0xffffffffu, root);
       if (root) root_id[c] = b + __popc(m & ((1u << lane) - 1u));
       b += __popc(m);
@@ -348,6 +361,16 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
     // all of a thread's global reads of the box are issued before the first
     // shared-memory store (kGeoBlock threads, kGeoPer positions each)
     __syncthreads();
+    // Thread t loads box position t + r kGeoBlock counted in the cells'
+    // storage order (its first coordinate runs along the contiguous axis),
+    // so that the loads of a warp coalesce whatever the storage order; the
+    // shared-memory box itself is indexed in the caller's axes.
+    auto box_pos = [&](int b, int& i, int& j, int& k) {
+      const int k0 = b % GE, k1 = (b / GE) % GE, k2 = b / (GE * GE);
+      i = sel3(p.inv[0], k0, k1, k2);
+      j = sel3(p.inv[1], k0, k1, k2);
+      k = sel3(p.inv[2], k0, k1, k2);
+    };
     uint8_t tv[kGeoPer];
     R pv[kGeoPer];
 #pragma unroll
@@ -356,12 +379,13 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
       tv[r] = 4;  // outside the domain: solid
       pv[r] = R(0.0);
       if (b < GB) {
-        const int i = b % GE, j = (b / GE) % GE, k = b / (GE * GE);
+        int i, j, k;
+        box_pos(b, i, j, k);
         const int X = wrapc(ox + i, p.nx, p.per[0]);
         const int Y = wrapc(oy + j, p.ny, p.per[1]);
         const int Z = wrapc(oz + k, p.nz, p.per[2]);
         if (X >= 0 && Y >= 0 && Z >= 0) {
-          const int c = X + p.nx * (Y + p.ny * Z);
+          const int c = cidx(p, X, Y, Z);
           tv[r] = d.flags[c] & F_TYPE;
           pv[r] = R(d.phi[c]);
         }
@@ -371,8 +395,11 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
     for (int r = 0; r < kGeoPer; ++r) {
       const int b = threadIdx.x + r * kGeoBlock;
       if (b < GB) {
-        styp[b] = tv[r];
-        sphi[b] = tv[r] >= T_OBST ? kObstacle<R>() : pv[r];
+        int i, j, k;
+        box_pos(b, i, j, k);
+        const int bs = i + GE * (j + GE * k);
+        styp[bs] = tv[r];
+        sphi[bs] = tv[r] >= T_OBST ? kObstacle<R>() : pv[r];
       }
     }
     __syncthreads();
@@ -470,7 +497,7 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
       if (X >= p.nx || Y >= p.ny || Z >= p.nz) continue;
       const int b = i + GE * (j + GE * k);
       if (styp[b] != T_IFACE) continue;
-      const int c = X + p.nx * (Y + p.ny * Z);
+      const int c = cidx(p, X, Y, Z);
       auto nh = [&](int a, int ii, int jj, int kk) {
         return snh[a * GN * GN * GN + (ii - 2) + GN * ((jj - 2) + GN * (kk - 2))];
       };
@@ -577,9 +604,10 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     R fx[Q], f[Q];
     unsigned miss = 0u;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) fx[i] = load_w<S, Q>(A[(long long)i * Np + c], i);
+    for (int i = 0; i < Q; ++i) fx[i] = load_own<Q, S>(A, Np, c, i);
+    f[0] = fx[0];  // the rest PDF stays in the cell
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
       const int st = nt[OPP(i)];
       const int src = nid[OPP(i)];
       if (st == T_GAS) miss |= 1u << i;
@@ -677,6 +705,11 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
         }
       }
     }
+    double s_in = 0.0;  // the mass-conserving formats: sum of the received values
+    if constexpr (S::kExactRest) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) s_in += (double)f[i];
+    }
     double rho = collide_any<Q, S, COLL>(f, p, bad);
     // moments of the stored post-collision PDFs, in post_moments' arithmetic
     // (new interface cells average them over their neighbours)
@@ -686,12 +719,24 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       // values): the mass a conversion to liquid hands over to them
       double sd = 0.0;
       R fs[Q];
+      if constexpr (S::kExactRest) {
+        store_cell<Q, S>(B, Np, c, f, s_in);
+        const double r0 = rest_slice<Q, S>(B, Np)[c];
+        fs[0] = (R)r0;
+        sd = r0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const T v = S::stored(f[i]);
-        B[(long long)i * Np + c] = v;
-        fs[i] = S::loadd(v);
-        sd += (double)fs[i];
+        for (int i = 1; i < Q; ++i) {
+          fs[i] = S::loadd(S::stored(f[i]));
+          sd += (double)fs[i];
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const T v = S::stored(f[i]);
+          B[(long long)i * Np + c] = v;
+          fs[i] = S::loadd(v);
+          sd += (double)fs[i];
+        }
       }
       rho = 1.0 + sd;
       R r0, jx0, jy0, jz0;
@@ -1043,8 +1088,8 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
         fn[i] = feq_dev<Q, R>(i, R(rb - 1.0), R(rb), R(ub0), R(ub1), R(ub2));
       else
         fn[i] = feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2));
-      B[(long long)i * Np + c] = store_w<S, Q>(fn[i], i);
     }
+    store_cell<Q, S>(B, Np, c, fn, rb - 1.0);
     if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, wm, (fl & F_WRAP) != 0, fn);
     const double m = 0.0 + s;
     d.mass[c] = m;
@@ -1291,24 +1336,64 @@ static __global__ void k_obs_final(const double* part, int nblocks, double* out)
   out[f] = a;
 }
 
-// PDFs of the current buffer as FP64 (zero on gas and obstacle cells).
+// PDFs of the current buffer as FP64 (zero on gas and obstacle cells), in
+// the caller's cell order: thread e writes the cell with caller index e.
 template <int Q, class S>
 __global__ void k_pdf_out(DPtrs d, KParams p, int parity, double* out) {
   using R = typename S::Real;
   const typename S::T* P = (const typename S::T*)d.pdf[parity];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= p.N) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.N) return;
+  const int c = storage_of_ext(p, e);
   const int t = d.flags[c] & F_TYPE;
   const bool fluid = (t == T_LIQ || t == T_IFACE);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     double v;
+    if constexpr (S::kExactRest) {
+      if (i == 0) {
+        out[(long long)i * p.N + e] = fluid ? rest_slice<Q, S>(P, p.Np)[c] + W<Q, double>(0) : 0.0;
+        continue;
+      }
+    }
     if constexpr (S::kDev)
       v = (double)S::loadd(P[(long long)i * p.Np + c]) + W<Q, double>(i);
     else
       v = (double)S::load(P[(long long)i * p.Np + c], W<Q, R>(i));
-    out[(long long)i * p.N + c] = fluid ? v : 0.0;
+    out[(long long)i * p.N + e] = fluid ? v : 0.0;
   }
+}
+
+// ------------------------------------------------------------ storage order
+// Liquid-holding kSegCells-cell groups of the storage order p over flags
+// given in the caller's order (one warp = one 32-cell group): the work list
+// length of the bulk sweep if the cells were stored that way.
+static __global__ void k_layout_census(const uint8_t* __restrict__ raw_ext, KParams p,
+                                       unsigned long long* groups) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool liq = c < p.N && raw_ext[ext_index(p, c)] == T_LIQ;
+  const unsigned b = __ballot_sync(0xffffffffu, liq);
+  if ((threadIdx.x & 31) == 0 && b) {
+    int n = 0;
+    for (int g = 0; g < 32; g += kSegCells) n += ((b >> g) & (kSegCells == 32 ? 0xffffffffu : ((1u << kSegCells) - 1u))) != 0u;
+    atomicAdd(groups, (unsigned long long)n);
+  }
+}
+
+// Arrays between the caller's cell order and the storage order: ncomp
+// consecutive arrays of N entries each.
+template <class T>
+__global__ void k_to_storage(const T* __restrict__ ext, T* __restrict__ st, KParams p, int ncomp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const int e = ext_index(p, c);
+  for (int k = 0; k < ncomp; ++k) st[(long long)k * p.N + c] = ext[(long long)k * p.N + e];
+}
+template <class T>
+__global__ void k_to_caller(const T* __restrict__ st, T* __restrict__ ext, KParams p) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.N) return;
+  ext[e] = st[storage_of_ext(p, e)];
 }
 
 // ---------------------------------------------------------------- batches

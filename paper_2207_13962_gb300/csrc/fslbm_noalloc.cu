@@ -78,6 +78,10 @@ extern "C" fslbm_status fslbm_observables_noalloc(const fslbm_domain* domain, in
   p.nz = domain->nz;
   p.N = (int)N;
   p.Np = N;
+  {
+    const int identity[3] = {0, 1, 2};  // the caller's arrays: x contiguous
+    set_layout(p, identity);
+  }
   for (int a = 0; a < 3; ++a) p.g[a] = g[a];
   DPtrs d;
   std::memset(&d, 0, sizeof(d));

@@ -161,7 +161,7 @@ fslbm_status fslbm_server_create(const fslbm_server_config* cfg, fslbm_server** 
   if (!cfg || !out || cfg->max_active < 1 || cfg->chunk_steps < 1) return FSLBM_EINVAL;
   if (cfg->lattice != FSLBM_D3Q19 && cfg->lattice != FSLBM_D3Q27) return FSLBM_EINVAL;
   if (cfg->collision != FSLBM_SRT && cfg->collision != FSLBM_TRT) return FSLBM_EINVAL;
-  if (cfg->precision < FSLBM_FP64 || cfg->precision > FSLBM_BF16S) return FSLBM_EINVAL;
+  if (cfg->precision < FSLBM_FP64 || cfg->precision > FSLBM_FP16SMC) return FSLBM_EINVAL;
   fslbm_server* s = new (std::nothrow) fslbm_server();
   if (!s) return FSLBM_ENOMEM;
   s->cfg = *cfg;

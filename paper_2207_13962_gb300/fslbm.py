@@ -23,7 +23,7 @@ STATUS = {0: "FSLBM_OK", 1: "FSLBM_EINVAL", 2: "FSLBM_ENOMEM", 3: "FSLBM_ECUDA",
 LATTICE = {19: 19, 27: 27, "D3Q19": 19, "D3Q27": 27}
 COLLISION = {"SRT": 0, "TRT": 1}
 VARIANT = {"NBRC": 1, "NBKC": 2, "OM": 3, "OM3": 4}
-PRECISION = {"FP64": 0, "FP32": 1, "FP16S": 2, "BF16S": 3}
+PRECISION = {"FP64": 0, "FP32": 1, "FP16S": 2, "BF16S": 3, "FP32MC": 4, "FP16SMC": 5}
 
 
 class fslbm_domain(C.Structure):
@@ -80,7 +80,7 @@ _lock = threading.Lock()
 SYMBOLS = ["fslbm_params_default", "fslbm_create", "fslbm_init", "fslbm_step", "fslbm_sync",
            "fslbm_observables", "fslbm_read_fields", "fslbm_bubbles", "fslbm_set_timing",
            "fslbm_stage_times", "fslbm_save", "fslbm_load", "fslbm_interface_count", "fslbm_work_counts",
-           "fslbm_observables_noalloc", "fslbm_destroy", "fslbm_last_error", "fslbm_version",
+           "fslbm_observables_noalloc", "fslbm_set_axis_order", "fslbm_get_axis_order", "fslbm_destroy", "fslbm_last_error", "fslbm_version",
            "fslbm_batch_create", "fslbm_batch_step", "fslbm_batch_sync", "fslbm_batch_autotune",
            "fslbm_batch_set_tuning", "fslbm_batch_get_tuning", "fslbm_batch_launches",
            "fslbm_batch_destroy", "fslbm_batch_last_error", "fslbm_memory_estimate",
@@ -133,6 +133,10 @@ def load(build_if_missing: bool = True):
         lib.fslbm_observables_noalloc.argtypes = [C.POINTER(fslbm_domain), i, p, p, p, p, p,
                                                   C.POINTER(fslbm_obs), p]
         lib.fslbm_observables_noalloc.restype = i
+        lib.fslbm_set_axis_order.argtypes = [p, p]
+        lib.fslbm_set_axis_order.restype = i
+        lib.fslbm_get_axis_order.argtypes = [p, p]
+        lib.fslbm_get_axis_order.restype = i
         lib.fslbm_destroy.argtypes = [p]
         lib.fslbm_destroy.restype = None
         lib.fslbm_last_error.argtypes = [p]
@@ -197,7 +201,7 @@ class Context:
     def __init__(self, shape, periodic=(False, False, False), q=19, collision="TRT", variant="OM",
                  precision="FP32", omega=1.0, trt_magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), sigma=0.0,
                  eps_phi=1e-2, p_v0=1.0 / 3.0, om3_fallback="NBKC", bubble_model=False,
-                 stream=None):
+                 stream=None, axis_order=None):
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -224,11 +228,24 @@ class Context:
         if st != OK:
             raise FslbmError(st, "fslbm_create failed")
         self.h = h
+        if axis_order is not None:
+            self.set_axis_order(axis_order)
 
     def _check(self, st):
         if st != OK:
             raise FslbmError(st, self.lib.fslbm_last_error(self.h).decode())
         return st
+
+    def set_axis_order(self, order):
+        """Storage order for the next init: (contiguous axis, ..., slowest
+        axis) as axis numbers 0..2, or None to let init choose."""
+        arr = None if order is None else (C.c_int * 3)(*[int(a) for a in order])
+        self._check(self.lib.fslbm_set_axis_order(self.h, arr))
+
+    def axis_order(self):
+        arr = (C.c_int * 3)()
+        self._check(self.lib.fslbm_get_axis_order(self.h, arr))
+        return tuple(arr)
 
     def close(self):
         if getattr(self, "h", None):
