@@ -75,11 +75,14 @@ typedef enum {
  * rather than to |f|.  Fill level, mass, excess mass, the mass flux between
  * cells and bubble volumes are always FP64.
  * FSLBM_FP32MC and FSLBM_FP16SMC are the mass-conserving forms of FP32 and
- * FP16S: the q - 1 moving deviations lie on a fixed grid (2^-44 and 2^-39),
- * the rest deviation is stored in FP64 and takes up every rounding of the
- * collision, so each liquid cell keeps exactly the mass it received and the
- * liquid mass (Eq. nm-fslbm-mass) does not drift with the storage rounding.
- * They store 8 more bytes per cell and buffer than FP32 / FP16S. */
+ * FP16S: the q - 1 moving deviations lie on a fixed grid (steps of 2^-34 and
+ * 2^-30), the rest deviation is stored as an integer number of grid steps
+ * and takes up every rounding of the collision, so each liquid cell keeps
+ * exactly the mass it received and the liquid mass (Eq. nm-fslbm-mass) does
+ * not drift with the storage rounding.  FP32MC stores as many bytes as FP32,
+ * FP16SMC 2 more per cell and buffer than FP16S; deviations are bounded by
+ * |f_i - w_i| < 2^-3 (FP32MC) and < 2 (FP16SMC), beyond which a step reports
+ * FSLBM_EUNSTABLE. */
 typedef enum {
   FSLBM_FP64 = 0,
   FSLBM_FP32 = 1,
@@ -89,9 +92,20 @@ typedef enum {
   FSLBM_FP16SMC = 5
 } fslbm_precision;
 
+/* Boundary of each axis of the domain (the faces at its two ends).  Walls
+ * lie outside the domain: FSLBM_NO_SLIP bounces PDFs back (Sec. 2.1),
+ * FSLBM_FREE_SLIP reflects them specularly, reversing the wall-normal
+ * component (Sec. 2.1); a reflected PDF that comes from a gas cell is
+ * missing and the free-surface BC reconstructs it (Sec. 2.2, the paragraph
+ * after Eq. nm-fslbm-boundary-condition), and interface cells exchange mass
+ * with the mirror cell along the wall (Eq. nm-fslbm-mass-flux).  Obstacle
+ * cells inside the domain are always no-slip. */
+typedef enum { FSLBM_NO_SLIP = 0, FSLBM_PERIODIC = 1, FSLBM_FREE_SLIP = 2 } fslbm_boundary;
+
 typedef struct {
   int nx, ny, nz;     /* cells per axis, each >= 1                             */
-  int periodic[3];    /* nonzero: periodic axis; zero: no-slip walls outside  */
+  int periodic[3];    /* fslbm_boundary of each axis (1 = periodic; 0 = no-slip
+                         and 2 = free-slip walls outside the domain)          */
 } fslbm_domain;
 
 typedef struct {
@@ -106,6 +120,13 @@ typedef struct {
   int bubble_model;   /* 0: all gas at p_v0; 1: per-bubble volume tracking
                          (Eq. nm-fslbm-pressure-volume)                         */
   void* stream;       /* cudaStream_t for all work, NULL = default stream       */
+  double smagorinsky_cs; /* Smagorinsky constant C_S of the LES model of Sec. 2.1
+                         (Eqs. nm-lbm-turbulence-viscosity to
+                         nm-lbm-turublence-relaxation-time; paper: 0.1), 0: off.
+                         The local relaxation time is
+                         tau = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C_S^2 Qbar / rho)) / 2
+                         from the non-equilibrium momentum flux Qbar of the
+                         PDFs entering the collision; TRT keeps trt_magic  */
 } fslbm_params;
 
 /* Whole-domain observables (FP64 reductions on the device). */
@@ -120,7 +141,7 @@ typedef struct {
 } fslbm_obs;
 
 /* Defaults: omega 1, Lambda 3/16, g 0, sigma 0, eps_phi 1e-2, p_v0 1/3,
- * FP32, OM3 fallback NBKC, no bubble model, default stream. */
+ * FP32, OM3 fallback NBKC, no bubble model, default stream, no LES. */
 void fslbm_params_default(fslbm_params* p);
 
 /* Create a context for one domain (Sec. 2; Sec. 3 for bc_variant).

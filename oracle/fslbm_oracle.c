@@ -65,7 +65,28 @@
  *       order of their lowest cell index; interface cells take the lowest id
  *       of their gas neighbours; volume V = #gas + sum over interface (1-phi)
  *       accumulated in fixed point with 2^-32 resolution.
- *   R20 cells outside a non-periodic boundary act as no-slip obstacle cells.
+ *   R20 cells outside a non-periodic boundary act as no-slip obstacle cells,
+ *       unless the face is a free-slip wall (R22).
+ *   R21 Smagorinsky LES (Sec. 2.1, Eqs. nm-lbm-turbulence-viscosity to
+ *       nm-lbm-turublence-relaxation-time): tau = tau0 + tau_t with
+ *       tau_t = (sqrt(tau0^2 + 2 sqrt(2) (C_S dx)^2 Qbar / (rho c_s^4)) - tau0)/2,
+ *       the printed form "1/2 sqrt(...) - tau0" read with the 1/2 over both
+ *       terms (as printed, tau would be tau0/2 at zero strain);
+ *       Qbar = sqrt(2 sum_ab Q_ab Q_ab), Q_ab = sum_i c_ia c_ib (f_i - f^eq_i)
+ *       from the PDFs entering the collision; dx_LES = 1.  TRT keeps its
+ *       magic parameter: omega- follows from the adjusted omega+.  The Guo
+ *       prefactors use the adjusted rates.
+ *   R22 free-slip faces (Sec. 2.1: PDFs reflected specularly, the normal
+ *       component reversed): a PDF whose pull source lies across a free-slip
+ *       face comes from the mirror cell, whose coordinates along those axes
+ *       are the cell's own, with the direction's components along them
+ *       reversed.  If the mirror cell is gas, the PDF is missing and the
+ *       free-surface BC reconstructs it (Sec. 2.2, the paragraph after
+ *       Eq. nm-fslbm-boundary-condition); if it is an obstacle, it bounces
+ *       back.  The mass exchange (Eq. nm-fslbm-mass-flux) of an interface
+ *       cell runs over these wall links like over lattice links, so the
+ *       masses of interface cells keep track of the PDFs that move between
+ *       cells along a wall.
  *
  * R8 has one exception: a gas cell that becomes interface gets f^eq of the
  * mean density and velocity of its neighbours (R14), with no collision, so
@@ -126,6 +147,14 @@ static int make_lattice(int q, lattice* L) {
     }
   }
   return 0;
+}
+
+/* Index of the direction (cx, cy, cz) in L, -1 if absent. */
+static int dir_of(const lattice* L, int cx, int cy, int cz) {
+  int i;
+  for (i = 0; i < L->q; ++i)
+    if (L->c[i][0] == cx && L->c[i][1] == cy && L->c[i][2] == cz) return i;
+  return -1;
 }
 
 int orc_lattice(int q, int* c, double* w, int* opp) {
@@ -221,10 +250,36 @@ static void post_moments(const lattice* L, const double* f, long stride,
   u[2] = jz / r - 0.5 * g[2];
 }
 
-/* Collision (Eq. nm-lbm-collision with R1, R9, R10). */
+/* Relaxation rate adjusted by the Smagorinsky model (R21) from the
+ * non-equilibrium part of the PDFs entering the collision. */
+static double les_omega(const lattice* L, double omega, double cs,
+                        const double* fin, const double* feq, double rho) {
+  double qxx = 0.0, qyy = 0.0, qzz = 0.0, qxy = 0.0, qxz = 0.0, qyz = 0.0;
+  double q2, qbar, tau0, tau;
+  int i;
+  for (i = 0; i < L->q; ++i) {
+    double cx = L->c[i][0], cy = L->c[i][1], cz = L->c[i][2];
+    double d = fin[i] - feq[i];
+    qxx = qxx + cx * cx * d;
+    qyy = qyy + cy * cy * d;
+    qzz = qzz + cz * cz * d;
+    qxy = qxy + cx * cy * d;
+    qxz = qxz + cx * cz * d;
+    qyz = qyz + cy * cz * d;
+  }
+  q2 = qxx * qxx + qyy * qyy + qzz * qzz + 2.0 * (qxy * qxy + qxz * qxz + qyz * qyz);
+  qbar = sqrt(2.0 * q2);
+  tau0 = 1.0 / omega;
+  tau = 0.5 * (tau0 + sqrt(tau0 * tau0 + 2.0 * sqrt(2.0) * (cs * cs) * qbar /
+                                               (rho * (1.0 / 9.0))));
+  return 1.0 / tau;
+}
+
+/* Collision (Eq. nm-lbm-collision with R1, R9, R10; LES R21 when cs > 0). */
 static void collide(const lattice* L, int collision, double omega,
-                    double trt_magic, const double* g, const double* fin,
-                    double* fout, double* rho_out, double* u_out) {
+                    double trt_magic, double cs, const double* g,
+                    const double* fin, double* fout, double* rho_out,
+                    double* u_out) {
   double rho, u[3];
   double feq[27], src[27];
   int i;
@@ -236,6 +291,7 @@ static void collide(const lattice* L, int collision, double omega,
       src[i] = guo_i(L, i, u[0], u[1], u[2], Fx, Fy, Fz);
     }
   }
+  if (cs > 0.0) omega = les_omega(L, omega, cs, fin, feq, rho);
   if (collision == 0) {
     double pref = 1.0 - 0.5 * omega;
     for (i = 0; i < L->q; ++i)
@@ -264,12 +320,12 @@ static void collide(const lattice* L, int collision, double omega,
 }
 
 void orc_collide(int q, int collision, double omega, double trt_magic,
-                 const double* g, const double* fin, double* fout,
+                 double cs, const double* g, const double* fin, double* fout,
                  double* rho_u) {
   lattice L;
   double rho, u[3];
   if (make_lattice(q, &L)) return;
-  collide(&L, collision, omega, trt_magic, g, fin, fout, &rho, u);
+  collide(&L, collision, omega, trt_magic, cs, g, fin, fout, &rho, u);
   rho_u[0] = rho;
   rho_u[1] = u[0];
   rho_u[2] = u[1];
@@ -334,7 +390,8 @@ void orc_reconstruct(int q, const int* recon, double rho_g, const double* u,
 /* ------------------------------------------------------------------ domain */
 struct orc {
   lattice L;
-  int nx, ny, nz, per[3];
+  int nx, ny, nz, per[3], slip[3];
+  double cs; /* Smagorinsky constant, 0: no LES */
   long N;
   int collision, variant, om3_fallback, bubble_model;
   double omega, trt_magic, g[3], sigma, eps, pv0;
@@ -380,13 +437,48 @@ static void coords(const orc* o, long c, int* x, int* y, int* z) {
 /* flag of a neighbour, OBST outside the domain (R20) */
 static int nflag_of(const orc* o, long n) { return n < 0 ? OBST : o->flag[n]; }
 
+/* Pull source of direction k of cell (x, y, z) (Eq. nm-lbm-streaming): the
+ * cell x - c_k, whose PDF k arrives (*j = k).  Across a periodic face the
+ * source wraps; across a free-slip face it is the mirror image (R22): the
+ * coordinate along that axis stays the cell's own and the arriving PDF is
+ * the one with that component of c_k reversed.  -1 across a no-slip face. */
+static long pull_source(const orc* o, int x, int y, int z, int k, int* j) {
+  const lattice* L = &o->L;
+  int p[3], c[3], n[3], a;
+  p[0] = x;
+  p[1] = y;
+  p[2] = z;
+  n[0] = o->nx;
+  n[1] = o->ny;
+  n[2] = o->nz;
+  for (a = 0; a < 3; ++a) {
+    int s = p[a] - L->c[k][a];
+    c[a] = L->c[k][a];
+    if (s < 0 || s >= n[a]) {
+      if (o->per[a]) {
+        s = (s + n[a]) % n[a];
+      } else if (o->slip[a]) {
+        s = p[a];
+        c[a] = -c[a];
+      } else {
+        return -1;
+      }
+    }
+    p[a] = s;
+  }
+  *j = dir_of(L, c[0], c[1], c[2]);
+  return (long)p[0] + (long)o->nx * ((long)p[1] + (long)o->ny * (long)p[2]);
+}
+
 orc* orc_create(int nx, int ny, int nz, int per_x, int per_y, int per_z, int q,
                 int collision, int variant, int om3_fallback, int bubble_model,
                 double omega, double trt_magic, double gx, double gy, double gz,
-                double sigma, double eps_phi, double p_v0) {
+                double sigma, double eps_phi, double p_v0, double cs) {
   orc* o;
   long N;
   if (nx < 1 || ny < 1 || nz < 1 || (q != 19 && q != 27)) return NULL;
+  if (per_x < 0 || per_x > 2 || per_y < 0 || per_y > 2 || per_z < 0 || per_z > 2) return NULL;
+  if (!(cs >= 0.0)) return NULL;
   if (variant < 1 || variant > 4 || (om3_fallback != 1 && om3_fallback != 2))
     return NULL;
   o = (orc*)calloc(1, sizeof(orc));
@@ -395,9 +487,13 @@ orc* orc_create(int nx, int ny, int nz, int per_x, int per_y, int per_z, int q,
   o->nx = nx;
   o->ny = ny;
   o->nz = nz;
-  o->per[0] = per_x;
-  o->per[1] = per_y;
-  o->per[2] = per_z;
+  o->per[0] = per_x == 1;
+  o->per[1] = per_y == 1;
+  o->per[2] = per_z == 1;
+  o->slip[0] = per_x == 2;
+  o->slip[1] = per_y == 2;
+  o->slip[2] = per_z == 2;
+  o->cs = cs;
   N = (long)nx * ny * nz;
   o->N = N;
   o->collision = collision;
@@ -747,9 +843,11 @@ static void stream_collide(orc* o) {
     if (fl != LIQ && fl != IFACE) continue;
     coords(o, c, &x, &y, &z);
     for (i = 0; i < q; ++i) fx[i] = o->f[i * N + c];
-    /* pull streaming (Eq. nm-lbm-streaming) with bounce-back at obstacles */
+    /* pull streaming (Eq. nm-lbm-streaming) with bounce-back at obstacles
+     * and no-slip faces, specular reflection at free-slip faces (R22) */
     for (i = 0; i < q; ++i) {
-      long s = nbr(o, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
+      int j = i;
+      long s = pull_source(o, x, y, z, i, &j);
       int sf = nflag_of(o, s);
       miss[i] = 0;
       if (sf == OBST) {
@@ -762,7 +860,7 @@ static void stream_collide(orc* o) {
           fin[i] = fx[L->opp[i]]; /* unreachable while the layer is closed */
         }
       } else {
-        fin[i] = o->f[i * N + s];
+        fin[i] = o->f[j * N + s];
       }
     }
     if (fl == IFACE) {
@@ -772,13 +870,16 @@ static void stream_collide(orc* o) {
       post_moments(L, o->f + c, N, o->g, &rc, uc);
       select_R(L, o->variant, o->om3_fallback, nh, miss, recon);
       reconstruct(L, recon, o->rhog[c], uc, fx, fin);
-      /* mass exchange (Eq. nm-fslbm-mass-flux, R11, R12) */
+      /* mass exchange (Eq. nm-fslbm-mass-flux, R11, R12) with the cell n
+       * whose PDF arrives in direction ibar: the neighbour x + c_i, or its
+       * mirror image across a free-slip face (R22) */
       for (i = 1; i < q; ++i) {
-        long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
+        int j = L->opp[i];
+        long n = pull_source(o, x, y, z, L->opp[i], &j);
         int nf = nflag_of(o, n);
         double a, b;
         if (nf == GAS || nf == OBST) continue;
-        a = o->f[L->opp[i] * N + n];
+        a = o->f[j * N + n];
         b = fx[i];
         if (nf == LIQ) {
           dm = dm + (a - b);
@@ -789,7 +890,7 @@ static void stream_collide(orc* o) {
       }
       o->mn[c] = o->m[c] + dm;
     }
-    collide(L, o->collision, o->omega, o->trt_magic, o->g, fin, fout, &rho, u);
+    collide(L, o->collision, o->omega, o->trt_magic, o->cs, o->g, fin, fout, &rho, u);
     for (i = 0; i < q; ++i) o->fn[i * N + c] = fout[i];
     o->rho[c] = rho;
     if (fl == IFACE) o->phin[c] = o->mn[c] / rho;

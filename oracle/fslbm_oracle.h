@@ -23,13 +23,15 @@ extern "C" {
 typedef struct orc orc;
 
 /* q = 19 or 27 for whole-domain runs (9 is accepted only by the unit helpers).
- * collision: 0 SRT, 1 TRT.  variant: 1 NBRC, 2 NBKC, 3 OM, 4 OM3.
- * om3_fallback: 1 NBRC or 2 NBKC.  bubble_model: 0 constant p_v0, 1 per-bubble
- * volume tracking.  Returns NULL on bad arguments. */
+ * per_x, per_y, per_z: boundary of each axis, 0 no-slip walls, 1 periodic,
+ * 2 free-slip walls.  collision: 0 SRT, 1 TRT.  variant: 1 NBRC, 2 NBKC,
+ * 3 OM, 4 OM3.  om3_fallback: 1 NBRC or 2 NBKC.  bubble_model: 0 constant
+ * p_v0, 1 per-bubble volume tracking.  cs: Smagorinsky constant (0: no LES).
+ * Returns NULL on bad arguments. */
 orc* orc_create(int nx, int ny, int nz, int per_x, int per_y, int per_z, int q,
                 int collision, int variant, int om3_fallback, int bubble_model,
                 double omega, double trt_magic, double gx, double gy, double gz,
-                double sigma, double eps_phi, double p_v0);
+                double sigma, double eps_phi, double p_v0, double cs);
 void orc_destroy(orc* o);
 
 /* fill[N], flags[N] (0 gas 1 interface 2 liquid 3 obstacle), velocity[3N]
@@ -62,7 +64,7 @@ void orc_feq(int q, double rho, const double* u, double* feq);
 /* One collision of a single cell: fin[q] -> fout[q]; rho and u (with the
  * force shift) are returned in rho_u[4]. */
 void orc_collide(int q, int collision, double omega, double trt_magic,
-                 const double* g, const double* fin, double* fout,
+                 double cs, const double* g, const double* fin, double* fout,
                  double* rho_u);
 /* Reconstruction set R of one interface cell: miss[q] (1 = PDF streams from a
  * gas cell), nhat[3]; recon[q] receives 1 for i in R. */

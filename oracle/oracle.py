@@ -57,7 +57,7 @@ def _load(openmp: bool = False):
         lib = C.CDLL(build_oracle(openmp=openmp))
         d, i, p = C.c_double, C.c_int, C.c_void_p
         lib.orc_create.restype = p
-        lib.orc_create.argtypes = [i, i, i, i, i, i, i, i, i, i, i, d, d, d, d, d, d, d, d]
+        lib.orc_create.argtypes = [i, i, i, i, i, i, i, i, i, i, i, d, d, d, d, d, d, d, d, d]
         lib.orc_destroy.argtypes = [p]
         lib.orc_init.restype = i
         lib.orc_init.argtypes = [p, p, p, p, p]
@@ -74,7 +74,7 @@ def _load(openmp: bool = False):
         lib.orc_lattice.restype = i
         lib.orc_lattice.argtypes = [i, p, p, p]
         lib.orc_feq.argtypes = [i, d, p, p]
-        lib.orc_collide.argtypes = [i, i, d, d, p, p, p, p]
+        lib.orc_collide.argtypes = [i, i, d, d, d, p, p, p, p]
         lib.orc_select.argtypes = [i, i, i, p, p, p]
         lib.orc_reconstruct.argtypes = [i, p, d, p, p, p]
         lib.orc_k8_smooth.restype = d
@@ -110,14 +110,16 @@ def feq(q: int, rho: float, u) -> np.ndarray:
     return out
 
 
-def collide(q: int, collision: int, omega: float, trt_magic: float, g, fin):
-    """One cell collision; returns (f_out[q], rho, u[3])."""
+def collide(q: int, collision: int, omega: float, trt_magic: float, g, fin, cs: float = 0.0):
+    """One cell collision (Smagorinsky constant cs, 0: no LES); returns
+    (f_out[q], rho, u[3])."""
     lib = _load()
     g = np.ascontiguousarray(g, np.float64)
     fin = np.ascontiguousarray(fin, np.float64)
     out = np.zeros(q, np.float64)
     ru = np.zeros(4, np.float64)
-    lib.orc_collide(q, collision, float(omega), float(trt_magic), _ptr(g), _ptr(fin), _ptr(out), _ptr(ru))
+    lib.orc_collide(q, collision, float(omega), float(trt_magic), float(cs), _ptr(g), _ptr(fin), _ptr(out),
+                    _ptr(ru))
     return out, ru[0], ru[1:].copy()
 
 
@@ -162,7 +164,8 @@ class Oracle:
     """Whole-domain FP64 FSLBM run on one CPU thread.
 
     Parameters mirror the GPU library's create call: domain (nx, ny, nz),
-    periodic flags, q (19/27), collision ('SRT'/'TRT'), variant
+    boundary of each axis (``periodic``: 0 / False no-slip walls, 1 / True
+    periodic, 2 free-slip walls), q (19/27), collision ('SRT'/'TRT'), variant
     ('NBRC'/'NBKC'/'OM'/'OM3'), OM3 fallback, bubble model, omega, TRT magic
     parameter, gravity g[3], surface tension sigma, eps_phi, p_v0.
     ``openmp`` runs the stream-collide cell loop on all host threads (the
@@ -172,7 +175,7 @@ class Oracle:
     def __init__(self, nx, ny, nz, periodic=(False, False, False), q=19, collision="TRT",
                  variant="OM", om3_fallback="NBKC", bubble_model=False, omega=1.0,
                  trt_magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), sigma=0.0, eps_phi=1e-2,
-                 p_v0=1.0 / 3.0, openmp=False):
+                 p_v0=1.0 / 3.0, smagorinsky_cs=0.0, openmp=False):
         self._lib = _load(openmp)
         self.shape = (int(nx), int(ny), int(nz))
         self.N = int(nx) * int(ny) * int(nz)
@@ -180,11 +183,11 @@ class Oracle:
         col = {"SRT": 0, "TRT": 1}[collision] if isinstance(collision, str) else int(collision)
         var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         fb = VARIANTS[om3_fallback] if isinstance(om3_fallback, str) else int(om3_fallback)
-        h = self._lib.orc_create(int(nx), int(ny), int(nz), int(bool(periodic[0])),
-                                 int(bool(periodic[1])), int(bool(periodic[2])), self.q, col, var, fb,
+        h = self._lib.orc_create(int(nx), int(ny), int(nz), int(periodic[0]),
+                                 int(periodic[1]), int(periodic[2]), self.q, col, var, fb,
                                  int(bool(bubble_model)), float(omega), float(trt_magic),
                                  float(g[0]), float(g[1]), float(g[2]), float(sigma), float(eps_phi),
-                                 float(p_v0))
+                                 float(p_v0), float(smagorinsky_cs))
         if not h:
             raise ValueError("oracle: invalid parameters")
         self._h = h

@@ -1,7 +1,8 @@
 """Build the CUDA library ``libfslbm.so`` in-tree for sm_103a.
 
 Each translation unit under ``csrc/`` is compiled by its own nvcc process (in
-parallel); the FP64 engine is compiled with ``--fmad=false`` so its arithmetic
+parallel), and every engine (storage format and lattice) is an object of its
+own; the FP64 engines are compiled with ``--fmad=false`` so their arithmetic
 rounds exactly as written.  The shared library links the CUDA runtime
 dynamically so that it shares one runtime with PyTorch in the same process.
 """
@@ -18,16 +19,18 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfslbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = {
-    "fslbm_api.cu": [],
-    "fslbm_f64.cu": ["--fmad=false"],
-    "fslbm_f32.cu": [],
-    "fslbm_f16.cu": [],
-    "fslbm_mc.cu": [],
-    "fslbm_noalloc.cu": [],
-    "fslbm_batch.cu": [],
-    "fslbm_server.cu": [],
-}
+# (source, object, flags): the C-ABI units, then one engine per storage
+# format and lattice from fslbm_engine_inst.cu (the FP64 engine without
+# multiply-add contraction, so that it rounds exactly as written)
+ENGINES = [("f64", "StoreF64"), ("f32", "StoreF32"), ("f16s", "StoreF16S"), ("bf16s", "StoreBF16S"),
+           ("f32mc", "StoreF32MC"), ("f16smc", "StoreF16SMC")]
+SOURCES = [(f, f.replace(".cu", ".o"), []) for f in
+           ("fslbm_api.cu", "fslbm_noalloc.cu", "fslbm_batch.cu", "fslbm_server.cu")]
+for _name, _store in ENGINES:
+    for _q in (19, 27):
+        SOURCES.append(("fslbm_engine_inst.cu", f"engine_{_name}_q{_q}.o",
+                        [f"-DFSLBM_INST_NAME=ops_{_name}_q{_q}", f"-DFSLBM_INST_Q={_q}",
+                         f"-DFSLBM_INST_STORE={_store}"] + (["--fmad=false"] if _name == "f64" else [])))
 
 
 def nvcc() -> str:
@@ -62,8 +65,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         common += list(extra_flags)
 
     def compile_one(item):
-        src, flags = item
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        src, obj, flags = item
+        obj = os.path.join(BUILD, obj)
         cmd = [cc] + common + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -74,8 +77,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             print(r.stderr, flush=True)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES.items()))
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", "-rpath,/usr/local/cuda/lib64"]

@@ -112,7 +112,7 @@ cudaError_t build_graphs(fslbm_ctx* c) {
     c->ops.step(c->d, c->kp, par, c->band_grid, c->bulk_grid, c->cap_stream, nullptr, &c->fork);
     e = cudaStreamEndCapture(c->cap_stream, &g);
     if (e != cudaSuccess) return e;
-    e = prioritise_nodes(g, c->ops.bulk_fn[0], c->ops.bulk_fn[1]);
+    e = prioritise_nodes(g, c->ops.bulk_fn[coll_of(c->kp) | slip_bit(c->kp)], nullptr);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[par], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return e;
@@ -144,6 +144,7 @@ void fslbm_params_default(fslbm_params* p) {
   p->om3_fallback = FSLBM_NBKC;
   p->bubble_model = 0;
   p->stream = nullptr;
+  p->smagorinsky_cs = 0.0;
 }
 
 const char* fslbm_last_error(const fslbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -157,6 +158,9 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   if (N > 400LL * 1000 * 1000) return FSLBM_EINVAL;
   if (lattice != FSLBM_D3Q19 && lattice != FSLBM_D3Q27) return FSLBM_EINVAL;
   if (!valid_enum(collision, 0, 1) || !valid_enum(bc_variant, 1, 4)) return FSLBM_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!valid_enum(domain->periodic[a], FSLBM_NO_SLIP, FSLBM_FREE_SLIP)) return FSLBM_EINVAL;
+  if (!(params->smagorinsky_cs >= 0.0)) return FSLBM_EINVAL;
   if (!valid_enum(params->precision, 0, 5)) return FSLBM_EINVAL;
   if (params->om3_fallback != FSLBM_NBRC && params->om3_fallback != FSLBM_NBKC) return FSLBM_EINVAL;
   if (!(params->omega > 0.0 && params->omega < 2.0)) return FSLBM_EINVAL;
@@ -183,7 +187,10 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   k.nx = domain->nx;
   k.ny = domain->ny;
   k.nz = domain->nz;
-  for (int a = 0; a < 3; ++a) k.per[a] = domain->periodic[a] ? 1 : 0;
+  for (int a = 0; a < 3; ++a) {
+    k.per[a] = domain->periodic[a] == FSLBM_PERIODIC ? 1 : 0;
+    k.slip[a] = domain->periodic[a] == FSLBM_FREE_SLIP ? 1 : 0;
+  }
   k.N = (int)N;
   k.Np = (N + 63) / 64 * 64;
   k.omega = params->omega;
@@ -194,6 +201,8 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   }
   k.pref_p = 1.0 - 0.5 * k.omega;
   k.pref_m = 1.0 - 0.5 * k.om_m;
+  k.magic = params->trt_magic;
+  k.cs = params->smagorinsky_cs;
   for (int a = 0; a < 3; ++a) k.g[a] = params->g[a];
   k.sigma = params->sigma;
   k.eps = params->eps_phi;
@@ -218,7 +227,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   int bulk_per_sm = c->ops.bulk_blocks_per_sm - FSLBM_BULK_RESERVE;
   {
     int fit = 0;
-    const void* fn = c->ops.bulk_fn[k.collision == 0 ? 0 : 1];
+    const void* fn = c->ops.bulk_fn[coll_of(k) | slip_bit(k)];
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kBulkBlock, c->ops.bulk_smem) == cudaSuccess &&
         fit > 0 && fit < bulk_per_sm)
       bulk_per_sm = fit;
@@ -303,7 +312,7 @@ fslbm_status fslbm_memory_estimate(const fslbm_domain* domain, fslbm_lattice lat
   const size_t elem = precision == FSLBM_FP64 ? 8
                       : (precision == FSLBM_FP32 || precision == FSLBM_FP32MC) ? 4
                                                                                : 2;
-  const size_t rest = (precision == FSLBM_FP32MC || precision == FSLBM_FP16SMC) ? 8 : 0;
+  const size_t rest = (precision == FSLBM_FP32MC || precision == FSLBM_FP16SMC) ? 4 : 0;
   const size_t rs = precision == FSLBM_FP64 ? 8 : 4;
   const size_t n4 = (N + 3) / 4 * 4;
   const size_t ntiles =

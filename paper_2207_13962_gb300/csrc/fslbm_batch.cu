@@ -14,7 +14,7 @@ using namespace fslbm;
 struct fslbm_batch {
   std::vector<fslbm_ctx*> m;
   Ops ops;
-  int collision = 1;
+  int collision = 1;               // collision variant of the members (coll_of)
   cudaStream_t stream = nullptr;   // caller's stream (may be NULL)
   cudaStream_t cap = nullptr;      // capture stream
   Fork fork{nullptr, nullptr, nullptr};
@@ -48,7 +48,8 @@ fslbm_status bcuda(fslbm_batch* b, cudaError_t e, const char* where) {
 }
 
 int max_bulk_blocks(const fslbm_batch* b) {
-  return b->m[0]->prm.precision == FSLBM_FP64 ? 2 : kBulkMinBlocks32;
+  if (b->m[0]->prm.precision == FSLBM_FP64) return 2;
+  return (b->collision & 2) ? 3 : kBulkMinBlocks32;  // the Smagorinsky sweep is compiled for 3
 }
 
 cudaError_t capture(fslbm_batch* b) {
@@ -63,7 +64,7 @@ cudaError_t capture(fslbm_batch* b) {
                     b->sms * b->tune.bulk_blocks_per_sm, b->collision, b->cap, &b->fork);
   e = cudaStreamEndCapture(b->cap, &g);
   if (e != cudaSuccess) return e;
-  e = prioritise_nodes(g, b->ops.batch_bulk_fn[0], b->ops.batch_bulk_fn[1]);
+  e = prioritise_nodes(g, b->ops.batch_bulk_fn[b->collision], nullptr);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
   return e;
@@ -117,14 +118,18 @@ fslbm_status fslbm_batch_create(fslbm_ctx* const* members, int n, void* stream, 
       if (members[j] == members[k]) return FSLBM_EINVAL;
     const fslbm_ctx* a = members[0];
     const fslbm_ctx* c = members[k];
-    if (c->q != a->q || c->prm.precision != a->prm.precision || c->collision != a->collision)
+    if (c->q != a->q || c->prm.precision != a->prm.precision || coll_of(c->kp) != coll_of(a->kp))
       return FSLBM_EINVAL;
   }
   fslbm_batch* b = new (std::nothrow) fslbm_batch();
   if (!b) return FSLBM_ENOMEM;
   b->m.assign(members, members + n);
   b->ops = members[0]->ops;
-  b->collision = members[0]->collision;
+  b->collision = coll_of(members[0]->kp);
+  for (int k = 0; k < n; ++k) {
+    const KParams& kp = members[k]->kp;
+    if (kp.slip[0] | kp.slip[1] | kp.slip[2]) b->collision |= 4;  // free-slip faces
+  }
   b->stream = (cudaStream_t)stream;
   b->h_recs.resize((size_t)n);
   int dev = 0;

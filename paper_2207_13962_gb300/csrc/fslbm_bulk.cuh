@@ -43,19 +43,21 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
     int x, y, z;
     decode(p, c, x, y, z);
 #pragma unroll
-    for (int i = i0; i < Q; ++i) f[i] = load_w<S, Q>(A[pull_index_general<Q>(p, c, x, y, z, i)], i);
+    for (int i = i0; i < Q; ++i)
+      f[i] = load_w<S, Q>(A[pull_index_general<Q, coll_slip(COLL)>(p, d.flags, c, x, y, z, i)], i);
   }
-  double s_in = 0.0;
+  long long s_in = 0;
   if constexpr (S::kExactRest) {
-    // the received stored values, summed exactly
-    s_in = rest_slice<Q, S>(A, Np)[c];
-    f[0] = (R)s_in;
+    // the received stored values in grid steps, summed exactly
+    const int r0 = rest_slice<Q, S>(A, Np)[c];
+    f[0] = from_steps<S>(r0);
+    s_in = r0;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) s_in += (double)f[i];
+    for (int i = 1; i < Q; ++i) s_in += grid_steps32<S>(f[i]);
   }
   bool bad = false;
   collide_any<Q, S, COLL>(f, p, bad);
-  store_cell<Q, S>(B, Np, c, f, s_in);
+  store_cell<Q, S>(B, Np, c, f, s_in, bad);
   if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], general, f);
   if (bad) d.err[0] = 1;
 }
@@ -96,8 +98,8 @@ __device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int 
       for (int i = S::kExactRest ? 1 : 0; i < Q; ++i) B[(long long)i * p.Np + c] = S::store(R(0.0), W<Q, R>(i));
     }
     if constexpr (S::kExactRest) {
-      // the FP64 rest slice: 4 cells per 32-byte sector
-      if (((lm >> (lane & ~3)) & 0xfu) && t == T_GAS) rest_slice<Q, S>(d.pdf[parity ^ 1], p.Np)[c] = 0.0;
+      // the int32 rest slice: 8 cells per 32-byte sector
+      if (((lm >> (lane & ~7)) & 0xffu) && t == T_GAS) rest_slice<Q, S>(d.pdf[parity ^ 1], p.Np)[c] = 0;
     }
   }
 }
@@ -113,8 +115,16 @@ __device__ __forceinline__ void bulk_unit(const DPtrs& d, const KParams& p, int 
 #endif
 constexpr int kBulkChunk = FSLBM_BULK_DYN;
 
+// Resident blocks per SM a bulk sweep is compiled for: the FP32 engines
+// kBulkMinBlocks32 (64 registers), 3 with the Smagorinsky model (its
+// momentum flux needs more), the FP64 engine 2.
+template <class S, int COLL>
+constexpr int bulk_min_blocks() {
+  return sizeof(typename S::Real) == 4 ? (coll_les(COLL) ? 3 : kBulkMinBlocks32) : 2;
+}
+
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
+__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
     k_bulk(DPtrs d, KParams p, int parity) {
   constexpr int kGroups = 32 / kSegCells;
   const int nseg = d.counts[5];

@@ -1,7 +1,15 @@
 // TMA-staged variant of the bulk sweep (arXiv 2207.13962, Sec. 2.1), built
 // when FSLBM_BULK_TMA is 1 (off by default: on GB300 it is slower than the
 // direct sweep, see the comment below).  Same cells, same arithmetic and
-// the same stores as k_bulk.
+// the same stores as k_bulk, for the plain storage formats and collisions
+// without the Smagorinsky model.
+//
+// Not to be enabled as it stands: when a bounded wait on a stage's copies
+// gives up, the warp drains the copies it issued with waits that are bounded
+// too; if those give up as well, the block can exit while bulk copies into
+// its shared memory are still in flight, and they would land in the shared
+// memory of a block that starts later on the SM.  The timeout path must
+// first wait for every copy already issued before the variant is used.
 #pragma once
 
 #include "fslbm_bulk.cuh"

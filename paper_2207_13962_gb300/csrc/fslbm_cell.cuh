@@ -142,9 +142,30 @@ __device__ __forceinline__ void sums(const R* f, R& r, R& jx, R& jy, R& jz) {
     if (CZ(i) != 0) jz = jz + R(CZ(i)) * f[i];
 }
 
+// Collision variants: bit 0 TRT (else SRT), bit 1 the Smagorinsky model;
+// the interface kernels also carry bit 2: the domain has free-slip faces.
+__host__ __device__ constexpr bool coll_trt(int coll) { return (coll & 1) != 0; }
+__host__ __device__ constexpr bool coll_les(int coll) { return (coll & 2) != 0; }
+__host__ __device__ constexpr bool coll_slip(int coll) { return (coll & 4) != 0; }
+
+// Relaxation time of the Smagorinsky model (Sec. 2.1, Eqs.
+// nm-lbm-turbulence-viscosity to nm-lbm-turublence-relaxation-time):
+// tau = (tau0 + sqrt(tau0^2 + 2 sqrt(2) (C_S dx)^2 Qbar / (rho c_s^4))) / 2
+// with Qbar = sqrt(2 sum_ab Q_ab Q_ab) of the momentum flux
+// Q_ab = sum_i c_ia c_ib (f_i - f^eq_i) of the PDFs entering the collision
+// (dx = 1, c_s^4 = 1/9); the six independent Q_ab are given.
+template <class R>
+__device__ __forceinline__ R les_tau(R qxx, R qyy, R qzz, R qxy, R qxz, R qyz, R rho, R omega, R cs) {
+  const R q2 = qxx * qxx + qyy * qyy + qzz * qzz + R(2.0) * (qxy * qxy + qxz * qxz + qyz * qyz);
+  const R qbar = sqrt(R(2.0) * q2);
+  const R tau0 = R(1.0) / omega;
+  return R(0.5) * (tau0 + sqrt(tau0 * tau0 + R(2.0) * sqrt(R(2.0)) * (cs * cs) * qbar / (rho * (R(1.0) / R(9.0)))));
+}
+
 // Collision of one cell (Eqs. nm-lbm-collision, nm-lbm-velocity with
-// F = rho g, SRT relaxing towards f^eq, or TRT).  f is overwritten with f*.
-// Returns rho; sets unstable when |u|^2 >= c_s^2, rho <= 0 or NaN.
+// F = rho g, SRT relaxing towards f^eq, or TRT; with the Smagorinsky model
+// when coll_les(COLL)).  f is overwritten with f*.  Returns rho; sets
+// unstable when |u|^2 >= c_s^2, rho <= 0 or NaN.
 template <int Q, class R, int COLL>
 __device__ __forceinline__ R collide(R* f, const KParams& p, bool& unstable) {
   R rho, jx, jy, jz;
@@ -156,8 +177,25 @@ __device__ __forceinline__ R collide(R* f, const KParams& p, bool& unstable) {
   R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
   R usq = ux * ux + uy * uy + uz * uz;
   if (!(usq < R(1.0 / 3.0)) || !(rho > R(0.0))) unstable = true;
-  if (COLL == 0) {
-    const R om = R(p.omega), pref = R(p.pref_p);
+  R omega = R(p.omega);
+  if constexpr (coll_les(COLL)) {
+    // momentum flux of the non-equilibrium part, summed in direction order
+    R qxx = R(0.0), qyy = R(0.0), qzz = R(0.0), qxy = R(0.0), qxz = R(0.0), qyz = R(0.0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R cx = R(CX(i)), cy = R(CY(i)), cz = R(CZ(i));
+      const R dn = f[i] - feq_i<Q, R>(i, rho, ux, uy, uz);
+      qxx = qxx + cx * cx * dn;
+      qyy = qyy + cy * cy * dn;
+      qzz = qzz + cz * cz * dn;
+      qxy = qxy + cx * cy * dn;
+      qxz = qxz + cx * cz * dn;
+      qyz = qyz + cy * cz * dn;
+    }
+    omega = R(1.0) / les_tau<R>(qxx, qyy, qzz, qxy, qxz, qyz, rho, omega, R(p.cs));
+  }
+  if constexpr (!coll_trt(COLL)) {
+    const R om = omega, pref = coll_les(COLL) ? R(1.0) - R(0.5) * omega : R(p.pref_p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       R fe = feq_i<Q, R>(i, rho, ux, uy, uz);
@@ -167,7 +205,15 @@ __device__ __forceinline__ R collide(R* f, const KParams& p, bool& unstable) {
   } else {
     // TRT on the pairs (i, ibar): the symmetric parts are shared, the
     // antisymmetric parts change sign (same roundings as a per-i loop).
-    const R omp = R(p.omega), omm = R(p.om_m), prp = R(p.pref_p), prm = R(p.pref_m);
+    // With the model, omega- follows from the adjusted omega+ through the
+    // magic parameter.
+    R omp = R(p.omega), omm = R(p.om_m), prp = R(p.pref_p), prm = R(p.pref_m);
+    if constexpr (coll_les(COLL)) {
+      omp = omega;
+      omm = R(1.0) / (R(0.5) + R(p.magic) / (R(1.0) / omp - R(0.5)));
+      prp = R(1.0) - R(0.5) * omp;
+      prm = R(1.0) - R(0.5) * omm;
+    }
     {
       const R fe = feq_i<Q, R>(0, rho, ux, uy, uz);
       const R sr = guo_i<Q, R>(0, ux, uy, uz, Fx, Fy, Fz);
@@ -228,9 +274,37 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
   const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
   const float usq = ux * ux + uy * uy + uz * uz;
   if (!(usq < 1.0f / 3.0f) || !(rho > 0.f)) unstable = true;
-  const float omp = float(p.omega), prp = float(p.pref_p);
-  const float omm = COLL == 0 ? omp : float(p.om_m), prm = COLL == 0 ? prp : float(p.pref_m);
+  float omp = float(p.omega), prp = float(p.pref_p);
+  float omm = coll_trt(COLL) ? float(p.om_m) : omp, prm = coll_trt(COLL) ? float(p.pref_m) : prp;
   const float base = dr - 1.5f * rho * usq;
+  if constexpr (coll_les(COLL)) {
+    // momentum flux of the non-equilibrium part: the pair (i, ibar) shares
+    // c_a c_b, and d_i - e_i + d_ibar - e_ibar = d_i + d_ibar - 2 es (the
+    // antisymmetric parts cancel)
+    float qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const float cx = float(CX(i)), cy = float(CY(i)), cz = float(CZ(i));
+      const float cu = cx * ux + cy * uy + cz * uz;
+      const float es = W<Q, float>(i) * (base + 4.5f * rho * cu * cu);
+      const float dn = d[i] + d[i + 1] - 2.0f * es;
+      qxx += cx * cx * dn;
+      qyy += cy * cy * dn;
+      qzz += cz * cz * dn;
+      qxy += cx * cy * dn;
+      qxz += cx * cz * dn;
+      qyz += cy * cz * dn;
+    }
+    omp = 1.0f / les_tau<float>(qxx, qyy, qzz, qxy, qxz, qyz, rho, omp, float(p.cs));
+    prp = 1.0f - 0.5f * omp;
+    if constexpr (coll_trt(COLL)) {
+      omm = 1.0f / (0.5f + float(p.magic) / (1.0f / omp - 0.5f));
+      prm = 1.0f - 0.5f * omm;
+    } else {
+      omm = omp;
+      prm = prp;
+    }
+  }
   const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
   {
     const float w = W<Q, float>(0);
@@ -286,49 +360,92 @@ __device__ __forceinline__ typename S::T store_w(typename S::Real v, int i) {
 }
 
 // ------------------------------------------- mass-conserving formats
-// The FP64 rest slice that follows the q slices of a PDF buffer.
+// Grid exponent of a format (0 for the formats without exact rest).
+template <class S>
+__host__ __device__ constexpr int grid_shift() {
+  if constexpr (S::kExactRest) return S::kShift;
+  else return 0;
+}
+
+// The int32 rest slice (grid steps) that follows the q slices of a PDF buffer.
 template <int Q, class S>
-__device__ __forceinline__ double* rest_slice(const void* P, long long Np) {
-  return (double*)((typename S::T*)P + (long long)Q * Np);
+__device__ __forceinline__ int* rest_slice(const void* P, long long Np) {
+  return (int*)((typename S::T*)P + (long long)Q * Np);
+}
+// A working value (deviation) in grid steps, rounded to the nearest.
+template <class S>
+__device__ __forceinline__ long long grid_steps(float d) {
+  return __float2ll_rn(d * (float)(1LL << S::kShift));
+}
+// The same for a working value that is a stored value (exact, 32-bit).
+template <class S>
+__device__ __forceinline__ int grid_steps32(float d) {
+  return __float2int_rn(d * (float)(1LL << S::kShift));
 }
 template <class S>
-__device__ __forceinline__ double snap_rest(double d0) {
-  return snap_grid(d0, S::kGrid, 1.0 / S::kGrid);
+__device__ __forceinline__ float from_steps(long long n) {
+  return (float)n * (1.0f / (float)(1LL << S::kShift));
 }
 
 // Stores the post-collision PDFs f (working representation) of storage
-// cell c into buffer B.  For the mass-conserving formats s_in is the FP64
-// sum of the values the collision received: the rest deviation becomes
-// s_in minus the sum of the stored moving values (exact when the inputs
-// were stored values, as for liquid cells; rounded to the grid otherwise).
+// cell c into buffer B.  For the mass-conserving formats s_in is the sum of
+// the values the collision received, in grid steps: the rest deviation
+// becomes s_in minus the stored moving values (so the stored sum is s_in);
+// a rest outside the int32 range sets bad.
 template <int Q, class S>
 __device__ __forceinline__ void store_cell(typename S::T* B, long long Np, long long c,
-                                           const typename S::Real* f, double s_in) {
+                                           const typename S::Real* f, long long s_in, bool& bad) {
   if constexpr (S::kExactRest) {
-    double s_out = 0.0;
+    constexpr float kRange = 2147483648.0f / (float)(1LL << S::kShift);  // |d| bound of the grid
+    long long s_out = 0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
+      if (!(fabsf(f[i]) < kRange)) bad = true;
       const typename S::T v = S::stored(f[i]);
       B[(long long)i * Np + c] = v;
-      s_out += (double)S::loadd(v);
+      s_out += S::steps(v);
     }
-    rest_slice<Q, S>(B, Np)[c] = snap_rest<S>(s_in - s_out);
+    long long r = s_in - s_out;
+    if (r > 2147483647LL || r < -2147483647LL) {
+      bad = true;
+      r = r > 0 ? 2147483647LL : -2147483647LL;
+    }
+    rest_slice<Q, S>(B, Np)[c] = (int)r;
   } else {
     (void)s_in;
+    (void)bad;
 #pragma unroll
     for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
   }
 }
 
 // PDF i of storage cell c of buffer P in the working representation (the
-// rest PDF of the mass-conserving formats from its FP64 slice).
+// rest PDF of the mass-conserving formats from its grid steps).
 template <int Q, class S>
 __device__ __forceinline__ typename S::Real load_own(const typename S::T* P, long long Np, long long c,
                                                      int i) {
   if constexpr (S::kExactRest) {
-    if (i == 0) return (typename S::Real)rest_slice<Q, S>(P, Np)[c];
+    if (i == 0) return from_steps<S>(rest_slice<Q, S>(P, Np)[c]);
   }
   return load_w<S, Q>(P[(long long)i * Np + c], i);
+}
+
+// Sum of the stored PDFs (deviations) of storage cell c: FP64 for the
+// deviation formats, exact from the grid steps for the mass-conserving ones.
+template <int Q, class S>
+__device__ __forceinline__ double stored_sum(const typename S::T* P, long long Np, long long c,
+                                             const typename S::Real* f) {
+  if constexpr (S::kExactRest) {
+    long long n = rest_slice<Q, S>(P, Np)[c];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) n += S::steps(P[(long long)i * Np + c]);
+    return (double)n * (1.0 / (double)(1LL << S::kShift));
+  } else {
+    double sd = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sd += (double)f[i];
+    return sd;
+  }
 }
 
 // rho and u of a cell from its post-collision PDFs: rho u = sum c f* - F/2.
@@ -346,10 +463,7 @@ __device__ __forceinline__ void post_moments(const typename S::T* P, long long N
   sums<Q, R>(f, r, jx, jy, jz);
   R rr = r;
   if constexpr (S::kDev) {
-    double sd = 0.0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-      sd += (S::kExactRest && i == 0) ? rest_slice<Q, S>(P, Np)[c] : (double)f[i];
+    const double sd = stored_sum<Q, S>(P, Np, c, f);
     rho = 1.0 + sd;
     rr = R(rho);
   } else {
@@ -361,27 +475,81 @@ __device__ __forceinline__ void post_moments(const typename S::T* P, long long N
 }
 
 // ------------------------------------------------- bounce-back via obstacle slots
-// Slice-i index of the pull source of direction i of cell c at (x, y, z):
-// the neighbour x - c_i, wrapped across periodic faces, or the cell's own
-// slot ibar (bounce-back) when the source lies outside a non-periodic face.
+// Pull source of direction i of the cell at (x, y, z) (Eq. nm-lbm-streaming):
+// the cell x - c_i, wrapped across periodic faces, whose PDF i arrives
+// (j = i).  Across a free-slip face the source is the mirror image: the
+// coordinate along that axis stays the cell's own and the arriving PDF is
+// the one with that component of c_i reversed (the specular reflection of
+// Sec. 2.1).  Returns the source's storage index, or -1 across a no-slip
+// face (bounce-back).  mirrored: the source was reflected at a wall.
 template <int Q>
-__device__ __forceinline__ long long pull_index_general(const KParams& p, int c, int x, int y,
-                                                        int z, int i) {
+__device__ __forceinline__ int pull_source(const KParams& p, int x, int y, int z, int i, int& j,
+                                           bool& mirrored) {
   int X = x - CX(i), Y = y - CY(i), Z = z - CZ(i);
+  int m = 0;
   bool out = false;
   if (X < 0 || X >= p.nx) {
     if (p.per[0]) X = X < 0 ? X + p.nx : X - p.nx;
+    else if (p.slip[0]) X = x, m |= 1;
     else out = true;
   }
   if (Y < 0 || Y >= p.ny) {
     if (p.per[1]) Y = Y < 0 ? Y + p.ny : Y - p.ny;
+    else if (p.slip[1]) Y = y, m |= 2;
     else out = true;
   }
   if (Z < 0 || Z >= p.nz) {
     if (p.per[2]) Z = Z < 0 ? Z + p.nz : Z - p.nz;
+    else if (p.slip[2]) Z = z, m |= 4;
     else out = true;
   }
-  return out ? (long long)OPP(i) * p.Np + c : (long long)i * p.Np + cidx(p, X, Y, Z);
+  j = m ? (int)kReflect.j[i][m] : i;
+  mirrored = m != 0;
+  return out ? -1 : cidx(p, X, Y, Z);
+}
+
+// Index (slice and cell) of the value a liquid cell c at (x, y, z) pulls in
+// direction i: its source's PDF (wrapped across periodic faces; with SLIP,
+// reflected at free-slip faces), or its own PDF ibar (bounce-back) when the
+// source lies across a no-slip face or the mirror image across a free-slip
+// face is an obstacle cell.  Without SLIP the free-slip logic is not
+// compiled (domains without free-slip faces).
+template <int Q, bool SLIP>
+__device__ __forceinline__ long long pull_index_general(const KParams& p, const uint8_t* flags, int c,
+                                                        int x, int y, int z, int i) {
+  if constexpr (SLIP) {
+    int j;
+    bool mir;
+    const int s = pull_source<Q>(p, x, y, z, i, j, mir);
+    if (s < 0 || (mir && (flags[s] & F_TYPE) == T_OBST)) return (long long)OPP(i) * p.Np + c;
+    return (long long)j * p.Np + s;
+  } else {
+    int X = x - CX(i), Y = y - CY(i), Z = z - CZ(i);
+    bool out = false;
+    if (X < 0 || X >= p.nx) {
+      if (p.per[0]) X = X < 0 ? X + p.nx : X - p.nx;
+      else out = true;
+    }
+    if (Y < 0 || Y >= p.ny) {
+      if (p.per[1]) Y = Y < 0 ? Y + p.ny : Y - p.ny;
+      else out = true;
+    }
+    if (Z < 0 || Z >= p.nz) {
+      if (p.per[2]) Z = Z < 0 ? Z + p.nz : Z - p.nz;
+      else out = true;
+    }
+    return out ? (long long)OPP(i) * p.Np + c : (long long)i * p.Np + cidx(p, X, Y, Z);
+  }
+}
+
+// Slot of the obstacle pull source x - c_i (inside the domain or across a
+// periodic face) that a fluid cell's reflected copy goes to.
+template <int Q>
+__device__ __forceinline__ long long obstacle_slot(const KParams& p, int x, int y, int z, int i) {
+  const int X = wrapc(x - CX(i), p.nx, p.per[0]);
+  const int Y = wrapc(y - CY(i), p.ny, p.per[1]);
+  const int Z = wrapc(z - CZ(i), p.nz, p.per[2]);
+  return (long long)i * p.Np + cidx(p, X, Y, Z);
 }
 
 // Reflected copies of a fluid cell's post-collision PDFs (working
@@ -395,7 +563,7 @@ __device__ __forceinline__ void write_reflected(const DPtrs& d, const KParams& p
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     if (!((wm >> i) & 1u)) continue;
-    const long long idx = general ? pull_index_general<Q>(p, c, x, y, z, i) : p.dofs[i] + c;
+    const long long idx = general ? obstacle_slot<Q>(p, x, y, z, i) : p.dofs[i] + c;
     B[idx] = store_w<S, Q>(f[OPP(i)], i);
   }
 }

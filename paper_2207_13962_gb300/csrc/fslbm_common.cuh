@@ -133,32 +133,31 @@ struct StoreBF16S {
 };
 
 // Mass-conserving variants of the FP32 and FP16 deviation formats.  The
-// q - 1 moving deviations are stored as in the base format but lie on the
-// grid of multiples of 2^-kGrid (FP32 values are rounded to it; FP16 values
-// d 2^15 are multiples of the smallest subnormal 2^-24, so d is a multiple
-// of 2^-39 already), and the rest deviation d_0 is stored in FP64, on the
-// same grid, in a slice of its own after the q slices of the buffer.  A
-// collision stores d_0 = (sum of the stored values it received) - (sum of
-// the q - 1 moving values it stores).  Every term is a multiple of 2^-kGrid
-// far below 2^53 of them, so both sums and the difference are exact in
-// FP64: a liquid cell's stored sum (its density) is exactly the one it
-// received, streaming and bounce-back move stored values unchanged, and
-// the total mass of the liquid does not drift.
-__device__ __forceinline__ float snap_grid(float d, float scale, float inv) {
-  return rintf(d * scale) * inv;  // both products are exact (powers of 2)
-}
-__device__ __forceinline__ double snap_grid(double d, double scale, double inv) {
-  return rint(d * scale) * inv;
-}
+// q - 1 moving deviations are stored as in the base format, but only values
+// on the grid of multiples of 2^-kShift: FP32 values are rounded to it, and
+// FP16 values (d 2^15) keep their own rounding where its step is coarser
+// than the grid and are rounded to the grid below.  Every stored value is
+// then an integer number of grid steps, and the rest deviation d_0 is stored
+// as that integer (int32) in a slice of its own after the q slices of the
+// buffer.  A collision stores d_0 = (sum of the stored values it received)
+// - (sum of the q - 1 moving values it stores), computed in integers: a
+// liquid cell's stored sum (its density) is exactly the one it received,
+// streaming and bounce-back move stored values unchanged, and the liquid's
+// total mass does not drift.  The sums run in integer arithmetic (no FP64,
+// whose rate is low on this GPU).  The grid bounds the deviations to
+// |d| < 2^(31 - kShift) (2^-3 for FP32MC, 2 for FP16SMC); a value beyond is
+// reported as an instability.
 struct StoreF32MC {
   using T = float;
   using Real = float;
   static constexpr int code = 4;
   static constexpr bool kDev = true;
   static constexpr bool kExactRest = true;
-  static constexpr double kGrid = 0x1p44;  // grid 2^-44
+  static constexpr int kShift = 34;
   __device__ static __forceinline__ float loadd(T v) { return v; }
-  __device__ static __forceinline__ T stored(float d) { return snap_grid(d, 0x1p44f, 0x1p-44f); }
+  __device__ static __forceinline__ T stored(float d) { return rintf(d * 0x1p34f) * 0x1p-34f; }
+  // the stored value in grid steps (exact: |v| 2^34 < 2^31 on the grid)
+  __device__ static __forceinline__ int steps(T v) { return __float2int_rn(v * 0x1p34f); }
   __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
   __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
 };
@@ -168,9 +167,14 @@ struct StoreF16SMC {
   static constexpr int code = 5;
   static constexpr bool kDev = true;
   static constexpr bool kExactRest = true;
-  static constexpr double kGrid = 0x1p39;  // grid 2^-39
+  static constexpr int kShift = 30;
   __device__ static __forceinline__ float loadd(T v) { return __half2float(v) * 0x1p-15f; }
-  __device__ static __forceinline__ T stored(float d) { return __float2half_rn(d * 0x1p15f); }
+  __device__ static __forceinline__ T stored(float d) {
+    const float x = d * 0x1p15f;  // the value held in FP16
+    // below 2^-4 the FP16 step is finer than the grid step 2^-15 of x
+    return fabsf(x) < 0.0625f ? __float2half_rn(rintf(x * 0x1p15f) * 0x1p-15f) : __float2half_rn(x);
+  }
+  __device__ static __forceinline__ int steps(T v) { return __float2int_rn(__half2float(v) * 0x1p15f); }
   __device__ static __forceinline__ Real load(T v, Real w) { return loadd(v) + w; }
   __device__ static __forceinline__ T store(Real f, Real w) { return stored(f - w); }
 };
@@ -213,6 +217,31 @@ constexpr int kBulkMinBlocks32 = FSLBM_BULK_MINB;
 constexpr int kSegCells = FSLBM_SEG_CELLS;
 static_assert(kSegCells == 8 || kSegCells == 16 || kSegCells == 32, "segment size");
 
+// Direction whose components are those of direction i with the ones along
+// the axes in mask (bit 0 x, 1 y, 2 z) reversed: the specular image of i at
+// walls normal to those axes.
+struct ReflectTable {
+  signed char j[27][8];
+};
+__host__ __device__ constexpr int dir_of_code(int code) {
+  int r = -1;
+  for (int i = 0; i < 27; ++i)
+    if (dcode(i) == code) r = i;
+  return r;
+}
+__host__ __device__ constexpr ReflectTable make_reflect_table() {
+  ReflectTable t{};
+  for (int i = 0; i < 27; ++i)
+    for (int m = 0; m < 8; ++m) {
+      const int cx = (m & 1) ? -CX(i) : CX(i);
+      const int cy = (m & 2) ? -CY(i) : CY(i);
+      const int cz = (m & 4) ? -CZ(i) : CZ(i);
+      t.j[i][m] = (signed char)dir_of_code((cx + 1) + 3 * (cy + 1) + 9 * (cz + 1));
+    }
+  return t;
+}
+__constant__ constexpr ReflectTable kReflect = make_reflect_table();
+
 // ----------------------------------------------------------- parameters
 // Storage order of the cells.  The caller's coordinates (x, y, z) and cell
 // index x + nx (y + ny z) are fixed; inside the library any axis may be the
@@ -230,10 +259,13 @@ struct KParams {
   int off[27];         // storage-index offset of direction i: c_i . (sx, sy, sz)
   long long dofs[27];  // i * Np - off[i]: pull source of interior cells
   int nx, ny, nz;
-  int per[3];
+  int per[3];   // periodic axes
+  int slip[3];  // axes with free-slip walls (specular reflection) outside
   int N;        // cells
   long long Np; // padded cells per PDF direction slice
   double omega, om_m, pref_p, pref_m;  // SRT: pref_p = 1 - omega/2
+  double magic;  // TRT magic parameter (omega- of the LES-adjusted omega+)
+  double cs;     // Smagorinsky constant, 0: no LES
   double g[3];
   double sigma, eps, pv0;
   int variant, om3_fb, bubble_model, collision;

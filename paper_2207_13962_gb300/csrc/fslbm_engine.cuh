@@ -4,9 +4,31 @@
 #pragma once
 
 #include "fslbm_internal.h"
+#include <type_traits>
+
 #include "fslbm_kernels.cuh"
 
 namespace fslbm {
+
+// Calls f with the collision variant as a compile-time constant
+// (bit 0: TRT, bit 1: Smagorinsky model, bit 2: free-slip faces).
+template <class F>
+inline void with_coll(int coll, F&& f) {
+  switch (coll) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    default: f(std::integral_constant<int, 7>{}); break;
+  }
+}
+
+// The kernels' variant: the collision variant and, in bit 2, whether the
+// domain has free-slip faces (the free-slip logic is compiled only then).
+inline int iface_coll(const KParams& p) { return coll_of(p) | slip_bit(p); }
 
 template <int Q, class S>
 struct Engine {
@@ -40,19 +62,17 @@ struct Engine {
   // reads post-collision PDFs of liquid cells.
   static void step(const DPtrs& d, const KParams& p, int parity, int band_grid, int bulk_grid,
                    cudaStream_t st, StageEvents* ev, const Fork* fk) {
+    const int coll = iface_coll(p);
     auto bulk = [&](cudaStream_t s2) {
-      if constexpr (kTmaBulk) {
-        constexpr size_t sm = tma_smem<Q, typename S::T>();
-        if (p.collision == 0)
-          k_bulk_tma<Q, S, 0><<<bulk_grid, kBulkBlock, sm, s2>>>(d, p, parity);
-        else
-          k_bulk_tma<Q, S, 1><<<bulk_grid, kBulkBlock, sm, s2>>>(d, p, parity);
-      } else {
-        if (p.collision == 0)
-          k_bulk<Q, S, 0><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
-        else
-          k_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
-      }
+      with_coll(coll, [&](auto C) {
+        constexpr int CO = decltype(C)::value;
+        if constexpr (kTmaBulk && !coll_les(CO)) {
+          constexpr size_t sm = tma_smem<Q, typename S::T>();
+          k_bulk_tma<Q, S, CO><<<bulk_grid, kBulkBlock, sm, s2>>>(d, p, parity);
+        } else {
+          k_bulk<Q, S, CO><<<bulk_grid, kBulkBlock, 0, s2>>>(d, p, parity);
+        }
+      });
     };
     const bool forked = fk && !ev;
     auto fork_bulk = [&]() {
@@ -67,10 +87,9 @@ struct Engine {
     if (ev) ev->mark(1, st);
     if (!forked) bulk(st);
     if (ev) ev->mark(2, st);
-    if (p.collision == 0)
-      k_interface<Q, S, 0><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
-    else
-      k_interface<Q, S, 1><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+    with_coll(coll, [&](auto C) {
+      k_interface<Q, S, decltype(C)::value><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+    });
     if (ev) ev->mark(3, st);
     k_resolve<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
     if (ev) ev->mark(4, st);
@@ -87,22 +106,22 @@ struct Engine {
 
   // One step of all domains of a block table.  Same stages and stream fork
   // as step(); the plan kernels lay out each phase's work on the device, and
-  // the last kernel swaps every domain's buffers.
+  // the last kernel swaps every domain's buffers.  collision: the variant
+  // shared by the members (coll_of), with bit 2 set when one of them has
+  // free-slip faces.
   static void batch_step(DomRec* recs, const BatchPlan& pl, int band_grid, int bulk_grid,
                          int collision, cudaStream_t st, const Fork* fk) {
     kb_plan_front<<<1, 1024, 0, st>>>(recs, pl);
     cudaEventRecord(fk->fork, st);
     cudaStreamWaitEvent(fk->side, fk->fork, 0);
-    if (collision == 0)
-      kb_bulk<Q, S, 0><<<bulk_grid, kBulkBlock, 0, fk->side>>>(recs, pl);
-    else
-      kb_bulk<Q, S, 1><<<bulk_grid, kBulkBlock, 0, fk->side>>>(recs, pl);
+    with_coll(collision, [&](auto C) {
+      kb_bulk<Q, S, decltype(C)::value><<<bulk_grid, kBulkBlock, 0, fk->side>>>(recs, pl);
+    });
     cudaEventRecord(fk->join, fk->side);
     kb_geometry<Q, S><<<band_grid * kGeoGridMult, kGeoBlock, geometry_smem<typename S::Real>(), st>>>(recs, pl);
-    if (collision == 0)
-      kb_interface<Q, S, 0><<<band_grid * 2, 128, 0, st>>>(recs, pl);
-    else
-      kb_interface<Q, S, 1><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+    with_coll(collision, [&](auto C) {
+      kb_interface<Q, S, decltype(C)::value><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+    });
     kb_resolve<Q><<<band_grid, kBlock, 0, st>>>(recs, pl);
     kb_count<Q><<<band_grid, kBlock, 0, st>>>(recs, pl);
     kb_plan_back<<<1, 1024, 0, st>>>(recs, pl);
@@ -146,7 +165,7 @@ struct Engine {
     o.pdf_out = &pdf_out;
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::Real);
-    o.rest_size = S::kExactRest ? sizeof(double) : 0;
+    o.rest_size = S::kExactRest ? sizeof(int) : 0;
     if constexpr (kTmaBulk) {
       o.bulk_fn[0] = (const void*)&k_bulk_tma<Q, S, 0>;
       o.bulk_fn[1] = (const void*)&k_bulk_tma<Q, S, 1>;
@@ -154,11 +173,23 @@ struct Engine {
       o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
       o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
     }
+    o.bulk_fn[2] = (const void*)&k_bulk<Q, S, 2>;
+    o.bulk_fn[3] = (const void*)&k_bulk<Q, S, 3>;
+    o.bulk_fn[4] = (const void*)&k_bulk<Q, S, 4>;
+    o.bulk_fn[5] = (const void*)&k_bulk<Q, S, 5>;
+    o.bulk_fn[6] = (const void*)&k_bulk<Q, S, 6>;
+    o.bulk_fn[7] = (const void*)&k_bulk<Q, S, 7>;
     o.bulk_blocks_per_sm = bulk_blocks_per_sm();
     o.bulk_smem = kTmaBulk ? tma_smem<Q, typename S::T>() : 0;
     o.batch_step = &batch_step;
     o.batch_bulk_fn[0] = (const void*)&kb_bulk<Q, S, 0>;
     o.batch_bulk_fn[1] = (const void*)&kb_bulk<Q, S, 1>;
+    o.batch_bulk_fn[2] = (const void*)&kb_bulk<Q, S, 2>;
+    o.batch_bulk_fn[3] = (const void*)&kb_bulk<Q, S, 3>;
+    o.batch_bulk_fn[4] = (const void*)&kb_bulk<Q, S, 4>;
+    o.batch_bulk_fn[5] = (const void*)&kb_bulk<Q, S, 5>;
+    o.batch_bulk_fn[6] = (const void*)&kb_bulk<Q, S, 6>;
+    o.batch_bulk_fn[7] = (const void*)&kb_bulk<Q, S, 7>;
     return o;
   }
 };

@@ -102,10 +102,12 @@ __global__ void k_init_cells(const uint8_t* __restrict__ raw, const double* __re
 #pragma unroll
     for (int i = 0; i < Q; ++i) fe[i] = feq_i<Q, R>(i, R(r), ux, uy, uz);
   }
-  // the mass-conserving formats store the density deviation r - 1 exactly
-  // (to their grid): the rest PDF takes up the rounding of the others
-  store_cell<Q, S>(P, p.Np, c, fe, r - 1.0);
-  store_cell<Q, S>(P2, p.Np, c, fe, r - 1.0);
+  // the mass-conserving formats store the density deviation r - 1 (to
+  // their grid): the rest PDF takes up the rounding of the others
+  bool over = false;
+  const long long s_in = S::kExactRest ? __double2ll_rn((r - 1.0) * (double)(1LL << grid_shift<S>())) : 0;
+  store_cell<Q, S>(P, p.Np, c, fe, s_in, over);
+  store_cell<Q, S>(P2, p.Np, c, fe, s_in, over);
   if (wm) {
     write_reflected<Q, S>(d, p, P, c, wm, (fl & F_WRAP) != 0, fe);
     write_reflected<Q, S>(d, p, P2, c, wm, (fl & F_WRAP) != 0, fe);
@@ -555,13 +557,13 @@ __global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) k_geometry(DPtrs d, 
 // ------------------------------------------------------- interface update
 // Directions whose neighbour data the mass exchange reads ahead at once, and
 // resident blocks of 128 threads per SM the FP32/FP16 interface kernels are
-// compiled for (the kernel is latency-bound: four blocks cap it at 128
-// registers a thread; the FP64 engine keeps two).
+// compiled for (the kernel is latency-bound: three blocks cap it at 168
+// registers a thread, which every variant fits without spilling; four
+// blocks at 128 registers measured 10 % slower on the Taylor bubble (118 vs
+// 107 us); the FP64 engine keeps two).  FSLBM_IFACE_MINB, when defined,
+// sets the bound for the FP32 and 16-bit engines.
 #ifndef FSLBM_IFACE_CHUNK
 #define FSLBM_IFACE_CHUNK 1
-#endif
-#ifndef FSLBM_IFACE_MINB
-#define FSLBM_IFACE_MINB 1
 #endif
 
 constexpr int kIfaceChunk = FSLBM_IFACE_CHUNK;
@@ -571,7 +573,14 @@ constexpr int kIfaceChunk = FSLBM_IFACE_CHUNK;
 // precision, so the sign alone would decide by rounding).  Exact in FP32
 // and FP64 alike.
 constexpr double kTie = 0x1p-20;
-constexpr int kIfaceMinBlocks = FSLBM_IFACE_MINB;
+template <class S, int COLL>
+constexpr int iface_min_blocks() {
+#ifdef FSLBM_IFACE_MINB
+  return sizeof(typename S::Real) == 4 ? FSLBM_IFACE_MINB : 2;
+#else
+  return sizeof(typename S::Real) == 4 ? 3 : 2;
+#endif
+}
 // Pull with the free-surface BC (Eq. nm-fslbm-boundary-condition) on the
 // variant's set R (Sec. 3), mass exchange (Eq. nm-fslbm-mass-flux) with
 // Thuerey's adjustment, fill update phi = m / rho, collision, marks.
@@ -592,13 +601,25 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     int x, y, z;
     decode(p, c, x, y, z);
     // neighbours x + c_i and their types (independent loads issued together);
-    // the pull source of direction i is the neighbour in direction ibar
+    // the pull source of direction i is the neighbour in direction ibar.  A
+    // cell beside a free-slip face links to the mirror image of a neighbour
+    // across it, whose PDF arrives with the wall-normal component reversed.
+    const bool slipface = coll_slip(COLL) && (flags[c] & F_FACE) && (p.slip[0] | p.slip[1] | p.slip[2]);
     int nid[Q];
     int nt[Q];
     nid[0] = c;
     nt[0] = T_IFACE;
+    if (!slipface) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) nid[i] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+      for (int i = 1; i < Q; ++i) nid[i] = nbr(p, x, y, z, CX(i), CY(i), CZ(i));
+    } else {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        int j;
+        bool mir;
+        nid[i] = pull_source<Q>(p, x, y, z, OPP(i), j, mir);
+      }
+    }
 #pragma unroll
     for (int i = 1; i < Q; ++i) nt[i] = ntype(flags, nid[i]);
     R fx[Q], f[Q];
@@ -612,7 +633,12 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       const int src = nid[OPP(i)];
       if (st == T_GAS) miss |= 1u << i;
       const bool fluid = (st == T_LIQ || st == T_IFACE);
-      const T v = A[(long long)(fluid ? i : OPP(i)) * Np + (fluid ? src : c)];
+      int j = i;  // the PDF that arrives in direction i
+      if (slipface) {
+        bool mir;
+        (void)pull_source<Q>(p, x, y, z, i, j, mir);
+      }
+      const T v = A[(long long)(fluid ? j : OPP(i)) * Np + (fluid ? src : c)];
       f[i] = load_w<S, Q>(v, i);
       if (st == T_GAS) f[i] = R(0.0);
     }
@@ -705,10 +731,10 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
         }
       }
     }
-    double s_in = 0.0;  // the mass-conserving formats: sum of the received values
+    long long s_in = 0;  // the mass-conserving formats: the received values in grid steps
     if constexpr (S::kExactRest) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) s_in += (double)f[i];
+      for (int i = 0; i < Q; ++i) s_in += grid_steps<S>(f[i]);
     }
     double rho = collide_any<Q, S, COLL>(f, p, bad);
     // moments of the stored post-collision PDFs, in post_moments' arithmetic
@@ -720,15 +746,17 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       double sd = 0.0;
       R fs[Q];
       if constexpr (S::kExactRest) {
-        store_cell<Q, S>(B, Np, c, f, s_in);
-        const double r0 = rest_slice<Q, S>(B, Np)[c];
-        fs[0] = (R)r0;
-        sd = r0;
+        store_cell<Q, S>(B, Np, c, f, s_in, bad);
+        const int r0 = rest_slice<Q, S>(B, Np)[c];
+        long long n = r0;
+        fs[0] = from_steps<S>(r0);
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
-          fs[i] = S::loadd(S::stored(f[i]));
-          sd += (double)fs[i];
+          const T v = S::stored(f[i]);
+          fs[i] = S::loadd(v);
+          n += S::steps(v);
         }
+        sd = (double)n * (1.0 / (double)(1LL << S::kShift));
       } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -774,7 +802,7 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
   }
 
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128, (sizeof(typename S::Real) == 4 ? kIfaceMinBlocks : 2)) k_interface(DPtrs d, KParams p, int parity) {
+__global__ void __launch_bounds__(128, (iface_min_blocks<S, COLL>())) k_interface(DPtrs d, KParams p, int parity) {
   const int n = d.counts[parity];
   bool bad = false;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
@@ -1089,7 +1117,10 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
       else
         fn[i] = feq_i<Q, R>(i, R(rb), R(ub0), R(ub1), R(ub2));
     }
-    store_cell<Q, S>(B, Np, c, fn, rb - 1.0);
+    bool over = false;
+    const long long s_new = S::kExactRest ? __double2ll_rn((rb - 1.0) * (double)(1LL << grid_shift<S>())) : 0;
+    store_cell<Q, S>(B, Np, c, fn, s_new, over);
+    if (over) d.err[0] = 1;
     if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, wm, (fl & F_WRAP) != 0, fn);
     const double m = 0.0 + s;
     d.mass[c] = m;
@@ -1352,7 +1383,9 @@ __global__ void k_pdf_out(DPtrs d, KParams p, int parity, double* out) {
     double v;
     if constexpr (S::kExactRest) {
       if (i == 0) {
-        out[(long long)i * p.N + e] = fluid ? rest_slice<Q, S>(P, p.Np)[c] + W<Q, double>(0) : 0.0;
+        out[(long long)i * p.N + e] =
+            fluid ? (double)rest_slice<Q, S>(P, p.Np)[c] * (1.0 / (double)(1LL << S::kShift)) + W<Q, double>(0)
+                  : 0.0;
         continue;
       }
     }
@@ -1454,7 +1487,7 @@ __device__ __forceinline__ int* batch_bulk_ctr(const BatchPlan& pl) { return pl.
 
 // Units of all domains handed out as in k_bulk, kBulkChunk at a time.
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2))
+__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
     kb_bulk(const DomRec* __restrict__ recs, BatchPlan pl) {
   const int total = pl.bulk[pl.n];
   auto unit = [&](int w) {
@@ -1478,7 +1511,7 @@ __global__ void __launch_bounds__(kBulkBlock, (sizeof(typename S::Real) == 4 ? k
 }
 
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(128, (sizeof(typename S::Real) == 4 ? kIfaceMinBlocks : 2)) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
+__global__ void __launch_bounds__(128, (iface_min_blocks<S, COLL>())) kb_interface(const DomRec* __restrict__ recs, BatchPlan pl) {
   const int total = pl.band[pl.n];
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     const int k = find_domain(pl.band, pl.n, g);

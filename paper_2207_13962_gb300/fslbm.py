@@ -34,7 +34,7 @@ class fslbm_params(C.Structure):
     _fields_ = [("omega", C.c_double), ("trt_magic", C.c_double), ("g", C.c_double * 3),
                 ("sigma", C.c_double), ("eps_phi", C.c_double), ("p_v0", C.c_double),
                 ("precision", C.c_int), ("om3_fallback", C.c_int), ("bubble_model", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("smagorinsky_cs", C.c_double)]
 
 
 class fslbm_tuning(C.Structure):
@@ -201,13 +201,14 @@ class Context:
     def __init__(self, shape, periodic=(False, False, False), q=19, collision="TRT", variant="OM",
                  precision="FP32", omega=1.0, trt_magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), sigma=0.0,
                  eps_phi=1e-2, p_v0=1.0 / 3.0, om3_fallback="NBKC", bubble_model=False,
-                 stream=None, axis_order=None):
+                 stream=None, axis_order=None, smagorinsky_cs=0.0):
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
         self.q = LATTICE[q]
+        # boundary of each axis: 0 / False no-slip, 1 / True periodic, 2 free-slip
         dom = fslbm_domain(self.shape[0], self.shape[1], self.shape[2],
-                           (C.c_int * 3)(*[int(bool(x)) for x in periodic]))
+                           (C.c_int * 3)(*[int(x) for x in periodic]))
         prm = fslbm_params()
         self.lib.fslbm_params_default(C.byref(prm))
         prm.omega = float(omega)
@@ -220,6 +221,7 @@ class Context:
         prm.om3_fallback = VARIANT[om3_fallback] if isinstance(om3_fallback, str) else int(om3_fallback)
         prm.bubble_model = int(bool(bubble_model))
         prm.stream = C.c_void_p(int(stream)) if stream else None
+        prm.smagorinsky_cs = float(smagorinsky_cs)
         self.precision = prm.precision
         h = C.c_void_p()
         col = COLLISION[collision] if isinstance(collision, str) else int(collision)
@@ -404,7 +406,7 @@ def _params_for(sc, precision, **over):
     lib = load()
     kw = dict(omega=sc.omega, g=sc.g, sigma=sc.sigma, bubble_model=sc.bubble_model)
     kw.update({k: v for k, v in over.items() if k in ("omega", "g", "sigma", "bubble_model", "trt_magic",
-                                                      "eps_phi", "p_v0", "om3_fallback")})
+                                                      "eps_phi", "p_v0", "om3_fallback", "smagorinsky_cs")})
     prm = fslbm_params()
     lib.fslbm_params_default(C.byref(prm))
     prm.omega = float(kw["omega"])
@@ -416,6 +418,8 @@ def _params_for(sc, precision, **over):
             setattr(prm, k, float(kw[k]))
     if "om3_fallback" in kw:
         prm.om3_fallback = VARIANT[kw["om3_fallback"]]
+    if "smagorinsky_cs" in kw:
+        prm.smagorinsky_cs = float(kw["smagorinsky_cs"])
     prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     return prm
 
@@ -448,7 +452,7 @@ class Server:
         vel = None if sc.velocity is None else np.ascontiguousarray(sc.velocity, np.float64)
         den = None if sc.density is None else np.ascontiguousarray(sc.density, np.float64)
         rq = fslbm_request()
-        rq.domain = fslbm_domain(*sc.shape, (C.c_int * 3)(*[int(bool(x)) for x in sc.periodic]))
+        rq.domain = fslbm_domain(*sc.shape, (C.c_int * 3)(*[int(x) for x in sc.periodic]))
         rq.bc_variant = VARIANT[over.get("variant", sc.variant)]
         rq.params = _params_for(sc, self.precision, **over)
         rq.fill, rq.flags = fill.ctypes.data, flags.ctypes.data

@@ -490,21 +490,30 @@ def test_gravity_wave_keeps_its_mirror_symmetry(variant):
     assert worst <= 1e-12, worst
 
 
-def test_normal_based_variants_are_ill_conditioned():
-    """NBRC and NBKC select their reconstructed PDFs by the sign of n.c_i
-    (Eqs. fsbcv-nbrc, fsbcv-nbkc), a discontinuous function of the normal;
-    beside the standing wave's trough the normal of these variants changes
-    sign every few steps.  Started from interface fill levels perturbed by
-    random 1e-6, the FP64 run of NBKC leaves its own trajectory by more than
-    1e-2 a(0) within 1000 steps, while OM and OM3, which select by the gas
-    neighbours alone (Eqs. fsbcv-om-sets, fsbcv-om3), answer linearly.  This
-    is why the reduced-precision runs of NBRC and NBKC cannot be held to an
-    observable bar against the FP64 trajectory."""
-    def amplitude_series(variant, pert):
+def test_gravity_wave_observable_conditioning():
+    """How far the FP64 oracle's own crest elevation a(t) = sum_j phi(0, j) - 32
+    moves within 1000 steps when the initial interface fill levels are
+    perturbed by random noise of a given size; this bounds what any
+    computation that differs from the oracle at that size can achieve on the
+    observable.
+
+    * NBRC / NBKC select their reconstructed PDFs by the sign of n.c_i
+      (Eqs. fsbcv-nbrc, fsbcv-nbkc), a discontinuous function of the normal,
+      and beside the standing wave's trough their normal changes sign every
+      few steps: at noise 1e-6 NBKC leaves its trajectory by more than
+      1e-2 a(0), while OM and OM3 (which select by the gas neighbours,
+      Eqs. fsbcv-om-sets, fsbcv-om3) answer linearly.
+    * At noise 1e-4 (the relative resolution of FP16 is 2^-11 = 4.9e-4) OM
+      too moves by more than 1e-2 a(0): a conversion threshold is crossed one
+      step earlier or later, and the crest column gains or loses a share of
+      excess mass for a while (the wave's amplitude is a third of a cell).
+    So the FP32 formats, whose rounding stays near 1e-6, are held to the 1e-3
+    bar for OM and OM3, and the others are reported."""
+    def amplitude_series(variant, pert, seed=1):
         sc = S.gravity_wave(variant=variant)
         fill = sc.fill.copy()
         m = sc.flags == S.IFACE
-        fill[m] += pert * np.random.default_rng(1).uniform(-1.0, 1.0, m.sum())
+        fill[m] += pert * np.random.default_rng(seed).uniform(-1.0, 1.0, m.sum())
         o = Oracle(*sc.shape, **S.make_oracle_kwargs(sc))
         o.init(fill, sc.flags, sc.velocity, sc.density)
         a = []
@@ -513,7 +522,9 @@ def test_normal_based_variants_are_ill_conditioned():
             a.append(o.read()["fill"].reshape(64, 32)[:, 0].sum() - 32.0)
         return np.array(a)
 
-    change = {v: float(np.abs(amplitude_series(v, 1e-6) - amplitude_series(v, 0.0)).max() / 0.32)
-              for v in ("NBKC", "OM", "OM3")}
-    assert change["NBKC"] > 1e-2, change
-    assert change["OM"] < 1e-5 and change["OM3"] < 1e-5, change
+    base = {v: amplitude_series(v, 0.0) for v in ("NBKC", "OM", "OM3")}
+    change = {(v, p): float(np.abs(amplitude_series(v, p) - base[v]).max() / 0.32)
+              for v, p in (("NBKC", 1e-6), ("OM", 1e-6), ("OM3", 1e-6), ("OM", 1e-4))}
+    assert change[("NBKC", 1e-6)] > 1e-2, change
+    assert change[("OM", 1e-6)] < 1e-5 and change[("OM3", 1e-6)] < 1e-5, change
+    assert change[("OM", 1e-4)] > 1e-2, change
