@@ -215,6 +215,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   k.om3_fb = params->om3_fallback;
   k.bubble_model = params->bubble_model ? 1 : 0;
   k.collision = (int)collision;
+  set_float_params(k);
 
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);

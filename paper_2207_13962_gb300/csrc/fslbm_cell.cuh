@@ -268,14 +268,14 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
     if (CZ(i) != 0) jz += float(CZ(i)) * d[i];
   }
   const float rho = 1.0f + dr;
-  const float gx = float(p.g[0]), gy = float(p.g[1]), gz = float(p.g[2]);
+  const float gx = p.fg[0], gy = p.fg[1], gz = p.fg[2];
   const float inv = __frcp_rn(rho);
   const float ux = jx * inv + 0.5f * gx, uy = jy * inv + 0.5f * gy, uz = jz * inv + 0.5f * gz;
   const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
   const float usq = ux * ux + uy * uy + uz * uz;
   if (!(usq < 1.0f / 3.0f) || !(rho > 0.f)) unstable = true;
-  float omp = float(p.omega), prp = float(p.pref_p);
-  float omm = coll_trt(COLL) ? float(p.om_m) : omp, prm = coll_trt(COLL) ? float(p.pref_m) : prp;
+  float omp = p.fomega, prp = p.fpref_p;
+  float omm = coll_trt(COLL) ? p.fom_m : omp, prm = coll_trt(COLL) ? p.fpref_m : prp;
   const float base = dr - 1.5f * rho * usq;
   if constexpr (coll_les(COLL)) {
     // momentum flux of the non-equilibrium part: the pair (i, ibar) shares
@@ -295,10 +295,10 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
       qxz += cx * cz * dn;
       qyz += cy * cz * dn;
     }
-    omp = 1.0f / les_tau<float>(qxx, qyy, qzz, qxy, qxz, qyz, rho, omp, float(p.cs));
+    omp = 1.0f / les_tau<float>(qxx, qyy, qzz, qxy, qxz, qyz, rho, omp, p.fcs);
     prp = 1.0f - 0.5f * omp;
     if constexpr (coll_trt(COLL)) {
-      omm = 1.0f / (0.5f + float(p.magic) / (1.0f / omp - 0.5f));
+      omm = 1.0f / (0.5f + p.fmagic / (1.0f / omp - 0.5f));
       prm = 1.0f - 0.5f * omm;
     } else {
       omm = omp;
@@ -469,9 +469,9 @@ __device__ __forceinline__ void post_moments(const typename S::T* P, long long N
   } else {
     rho = r;
   }
-  u[0] = jx / rr - R(0.5) * R(p.g[0]);
-  u[1] = jy / rr - R(0.5) * R(p.g[1]);
-  u[2] = jz / rr - R(0.5) * R(p.g[2]);
+  u[0] = jx / rr - R(0.5) * gpar<R>(p, 0);
+  u[1] = jy / rr - R(0.5) * gpar<R>(p, 1);
+  u[2] = jz / rr - R(0.5) * gpar<R>(p, 2);
 }
 
 // ------------------------------------------------- bounce-back via obstacle slots

@@ -267,6 +267,9 @@ struct KParams {
   double magic;  // TRT magic parameter (omega- of the LES-adjusted omega+)
   double cs;     // Smagorinsky constant, 0: no LES
   double g[3];
+  // FP32 copies of the parameters the FP32 engines use in every cell (a
+  // double-to-float conversion on the device runs on the FP64 pipe)
+  float fg[3], fomega, fom_m, fpref_p, fpref_m, fmagic, fcs;
   double sigma, eps, pv0;
   int variant, om3_fb, bubble_model, collision;
 };
@@ -297,6 +300,25 @@ inline void set_layout(KParams& k, const int ax[3]) {
 }
 
 inline bool is_identity_layout(const KParams& k) { return k.ax[0] == 0 && k.ax[1] == 1 && k.ax[2] == 2; }
+
+// Fills the FP32 copies of k's FP64 parameters (rounded to nearest, as a
+// device conversion would).
+inline void set_float_params(KParams& k) {
+  for (int a = 0; a < 3; ++a) k.fg[a] = (float)k.g[a];
+  k.fomega = (float)k.omega;
+  k.fom_m = (float)k.om_m;
+  k.fpref_p = (float)k.pref_p;
+  k.fpref_m = (float)k.pref_m;
+  k.fmagic = (float)k.magic;
+  k.fcs = (float)k.cs;
+}
+
+// Gravity component a in the arithmetic type R.
+template <class R>
+__device__ __forceinline__ R gpar(const KParams& p, int a) {
+  if constexpr (sizeof(R) == 4) return p.fg[a];
+  else return p.g[a];
+}
 
 // Device pointers of one domain.
 struct DPtrs {

@@ -705,9 +705,9 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
     R rc, jx, jy, jz;
     sums<Q, R>(fx, rc, jx, jy, jz);
     if constexpr (S::kDev) rc = R(1.0) + rc;
-    const R ux = jx / rc - R(0.5) * R(p.g[0]);
-    const R uy = jy / rc - R(0.5) * R(p.g[1]);
-    const R uz = jz / rc - R(0.5) * R(p.g[2]);
+    const R ux = jx / rc - R(0.5) * gpar<R>(p, 0);
+    const R uy = jy / rc - R(0.5) * gpar<R>(p, 1);
+    const R uz = jz / rc - R(0.5) * gpar<R>(p, 2);
     // set R of the variant (Sec. 3) and reconstruction; |n^.c_i| <= kTie
     // counts as a tie (n.c_i = 0): NBRC reconstructs ties, NBKC does not
     const R n0 = nhat[3LL * c], n1 = nhat[3LL * c + 1], n2 = nhat[3LL * c + 2];
@@ -770,18 +770,18 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       R r0, jx0, jy0, jz0;
       sums<Q, R>(fs, r0, jx0, jy0, jz0);
       const R rr = R(rho);
-      mu[0] = jx0 / rr - R(0.5) * R(p.g[0]);
-      mu[1] = jy0 / rr - R(0.5) * R(p.g[1]);
-      mu[2] = jz0 / rr - R(0.5) * R(p.g[2]);
+      mu[0] = jx0 / rr - R(0.5) * gpar<R>(p, 0);
+      mu[1] = jy0 / rr - R(0.5) * gpar<R>(p, 1);
+      mu[2] = jz0 / rr - R(0.5) * gpar<R>(p, 2);
       d.mom_rho[c] = rho;
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
       R r0, jx0, jy0, jz0;
       sums<Q, R>(f, r0, jx0, jy0, jz0);
-      mu[0] = jx0 / r0 - R(0.5) * R(p.g[0]);
-      mu[1] = jy0 / r0 - R(0.5) * R(p.g[1]);
-      mu[2] = jz0 / r0 - R(0.5) * R(p.g[2]);
+      mu[0] = jx0 / r0 - R(0.5) * gpar<R>(p, 0);
+      mu[1] = jy0 / r0 - R(0.5) * gpar<R>(p, 1);
+      mu[2] = jz0 / r0 - R(0.5) * gpar<R>(p, 2);
       d.mom_rho[c] = (double)r0;
     }
     {
@@ -1149,9 +1149,16 @@ __device__ __forceinline__ void apply_cell(const DPtrs& d, const KParams& p, int
 
 template <int Q, class S>
 __global__ void __launch_bounds__(128) k_apply(DPtrs d, KParams p, int parity) {
-  const int n = d.counts[parity] + d.counts[2];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    apply_cell<Q, S>(d, p, parity, k);
+  // the new interface cells (long dependent chains) are dealt round-robin
+  // over the blocks, cell j to thread j / G of block j mod G, so that they
+  // spread over all SMs instead of filling the first blocks; the band cells
+  // follow in order
+  const int nnew = d.counts[2];
+  const int total = gridDim.x * blockDim.x;
+  for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < nnew; j += total) apply_cell<Q, S>(d, p, parity, j);
+  const int nband = d.counts[parity];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nband; k += total)
+    apply_cell<Q, S>(d, p, parity, nnew + k);
 }
 
 // Fixed-point bubble-volume term round((1 - phi) 2^32).

@@ -83,6 +83,7 @@ extern "C" fslbm_status fslbm_observables_noalloc(const fslbm_domain* domain, in
     set_layout(p, identity);
   }
   for (int a = 0; a < 3; ++a) p.g[a] = g[a];
+  set_float_params(p);
   DPtrs d;
   std::memset(&d, 0, sizeof(d));
   d.pdf[0] = (void*)pdf;
