@@ -134,11 +134,12 @@ class ClockSampler:
 # what k_bulk is compiled from: its own header, the cell layer, the common
 # types and the build flags
 KERNEL_SOURCES = tuple("paper_2207_13962_gb300/" + f for f in (
-    "csrc/fslbm_bulk.cuh", "csrc/fslbm_cell.cuh", "csrc/fslbm_common.cuh", "build.py"))
+    "csrc/fslbm_bulk.cuh", "csrc/fslbm_cell.cuh", "csrc/fslbm_common.cuh", "csrc/fslbm_kernels.cuh", "build.py"))
 
 
 def kernel_source_hash() -> str:
-    """SHA-256 of the bulk sweep's sources (the ncu traffic applies only to them)."""
+    """SHA-256 of the fused geometry + bulk sweep's sources (the ncu traffic
+    applies only to them)."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -148,11 +149,12 @@ def kernel_source_hash() -> str:
 
 
 def bulk_traffic(n_liquid: float, precision: str):
-    """DRAM bytes per bulk launch from the committed ncu capture
-    (profiles/k_bulk_traffic.json), scaled by liquid cells; None when the
-    kernel sources changed since the capture or the precision differs."""
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture (profiles/k_bulk_geo_traffic.json), scaled by liquid cells; None
+    when the kernel sources changed since the capture or the precision
+    differs."""
     try:
-        with open(os.path.join(ROOT, "profiles", "k_bulk_traffic.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", "k_bulk_geo_traffic.json")) as fh:
             t = json.load(fh)
     except Exception:
         return None
@@ -308,16 +310,26 @@ def bench_ours(args, ws, rank, local):
 
     # ---- per-stage CUDA-event timing (kernels launched one by one on the
     # context's stream) for the roofline of the dominant kernel
+    wc1 = ctx.work_counts()
     ctx.set_timing(True)
     ctx.step(args.steps)
     times, _ = ctx.stage_times()
     ctx.set_timing(False)
     obs2 = ctx.observables()
+    wc2 = ctx.work_counts()
     bulk_ms = times["bulk"] / args.steps
     n_liq = 0.5 * (obs1["n_liquid"] + obs2["n_liquid"])
     # algorithmic bytes of one bulk launch: read + write q PDFs and read one
     # flag byte per liquid cell (the sweep visits liquid cells only)
     alg_bytes = n_liq * (2 * ((Q - (1 if prec in REST_BYTES else 0)) * S_BYTES[prec] + REST_BYTES.get(prec, 0)) + 1)
+    fused = prec != "FP64"
+    if fused:
+        # the FP32 and 16-bit engines run the geometry tiles in the same
+        # launch: each tile's 512 cells read once (FP64 fill level + flag),
+        # each interface cell's normal, gas density (FP32) and class written
+        tiles = 0.5 * (wc1["geometry_tiles"] + wc2["geometry_tiles"])
+        n_if = 0.5 * (wc1["interface_cells"] + wc2["interface_cells"])
+        alg_bytes += tiles * 512 * 9 + n_if * (4 * 4 + 1)
     achieved = alg_bytes / (bulk_ms * 1e-3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -411,12 +423,15 @@ def bench_ours(args, ws, rank, local):
                 "status": int(st),
             },
             "roofline": {
-                "bound": "hbm", "kernel": "k_bulk (pull stream-collide of liquid cells)",
+                "bound": "hbm",
+                "kernel": ("k_bulk_geo (geometry tiles, then the pull stream-collide of liquid cells, in one "
+                           "persistent launch)" if fused else "k_bulk (pull stream-collide of liquid cells)"),
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (hbm_gbs, burst copy)",
                 "traffic": (round(bulk_traffic(n_liq, prec)) if bulk_traffic(n_liq, prec) else None),
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
-                                "160x160x256 profiling case, scaled by liquid cells (profiles/k_bulk_traffic.json)",
+                                "160x160x256 profiling case, scaled by liquid cells "
+                                "(profiles/k_bulk_geo_traffic.json)",
                 "alg_bytes_per_launch": int(alg_bytes), "launch_ms": round(bulk_ms, 6),
                 "stage_share": share,
             },
@@ -455,6 +470,17 @@ def _crown(fill, flags, L):
     return float(top + f3[top][flags.reshape(L, L, L)[top] == S.IFACE].max())
 
 
+def _lifted(fill, sc):
+    """Drop impact: liquid volume above the undisturbed pool, the sum of the
+    fill level over the layers k >= depth + 2 (the drop's remnant and the
+    crown sheet).  An integral of the fill level, so it moves by about the
+    size of the fill levels' own error, unlike the crown height, which jumps
+    by a cell when one interface cell at the tip appears or empties."""
+    L = sc.shape[0]
+    k0 = int(np.ceil(sc.meta["depth"])) + 2
+    return float(fill.reshape(L, L, L)[k0:].sum())
+
+
 def bench_batch(args, emit=True):
     """64 cylindrical dam breaks of seeded uneven sizes (D3Q27 TRT): one at a
     time in plain FP32, as one batch in FP32 and as one batch in the reduced
@@ -482,7 +508,9 @@ def bench_batch(args, emit=True):
         return e0.elapsed_time(e1) * 1e-3
 
     def observe(ctxs):
-        return [(_front_radius(c.read(pdf=False)["fill"], sc.shape[0]), c.observables()["total_mass"])
+        # (floor-layer front radius, total mass, seed-fill maximum front radius)
+        return [(_front_radius(c.read(pdf=False)["fill"], sc.shape[0]), c.observables()["total_mass"],
+                 c.front(0, (sc.shape[0] / 2.0, sc.shape[1] / 2.0))["r_max"])
                 for sc, c in zip(scs, ctxs)]
 
     res, obs_at = {}, {}
@@ -512,7 +540,9 @@ def bench_batch(args, emit=True):
             "launches_per_step": (batch.launches() - l0) / steps,
             "mass_drift_rel_max": max(abs(o[1] - m) / m for o, m in zip(obs_at[prec], m0)),
             "front_radius_rel_err_vs_plain_fp32": max(abs(a[0] - b[0]) / max(b[0], 1e-30)
-                                                      for a, b in zip(obs_at[prec], ref))}
+                                                      for a, b in zip(obs_at[prec], ref)),
+            "seed_fill_rmax_rel_err_vs_plain_fp32": max(abs(a[2] - b[2]) / max(b[2], 1e-30)
+                                                        for a, b in zip(obs_at[prec], ref))}
         batch.close()
         for c in ctxs:
             c.close()
@@ -520,7 +550,8 @@ def bench_batch(args, emit=True):
                        f"{min(p['L'] for p in prm)}..{max(p['L'] for p in prm)} (seed 2207), D3Q27 TRT, "
                        f"g=1e-5, nu=1e-3, OM; {steps} timed steps after {total - steps}",
            "cells": cells, "unit": "MLUPS", "results": res,
-           "observable": "front radius sqrt(sum of floor-layer fill / pi), relative to the plain FP32 runs"}
+           "observable": "front radius sqrt(sum of floor-layer fill / pi), and the maximum radius of the "
+                         "floor layer's seed-fill front cells (fslbm_front), relative to the plain FP32 runs"}
     if emit:
         print(json.dumps({"metric": METRIC, "workload": "batched cylindrical dam breaks", **out,
                           "data": "synthetic (seeded generator, no dataset)"}), flush=True)
@@ -589,6 +620,7 @@ def bench_serve(args, emit=True):
 
     res, makespan = _serve_trace(scs, steps, fifo_submit, fifo_poll)
     ref = [_crown(res[k]["fill"], res[k]["flags"], scs[k][1].shape[0]) for k in range(len(scs))]
+    ref_v = [_lifted(res[k]["fill"], scs[k][1]) for k in range(len(scs))]
     ttr = [res[k]["t_result"] for k in range(len(scs))]
     out["plain_fp32_fifo"] = {"mlups": round(cells * steps / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
                               "p50_s": round(float(np.percentile(ttr, 50)), 4),
@@ -617,11 +649,14 @@ def bench_serve(args, emit=True):
         ttr = [res[k]["t_result"] for k in range(len(scs))]
         err = max(abs(_crown(res[k]["fill"], res[k]["flags"], scs[k][1].shape[0]) - ref[k]) / max(ref[k], 1e-30)
                   for k in range(len(scs)))
+        err_v = max(abs(_lifted(res[k]["fill"], scs[k][1]) - ref_v[k]) / max(ref_v[k], 1e-30)
+                    for k in range(len(scs)))
         st = srv.stats()
         out[f"served_{prec.lower()}"] = {
             "mlups": round(cells * steps / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
             "p50_s": round(float(np.percentile(ttr, 50)), 4), "p99_s": round(float(np.percentile(ttr, 99)), 4),
-            "crown_rel_err_vs_plain_fp32": err, "max_active_seen": st["max_active_seen"],
+            "crown_rel_err_vs_plain_fp32": err, "lifted_volume_rel_err_vs_plain_fp32": err_v,
+            "max_active_seen": st["max_active_seen"],
             "batch_rebuilds": st["batch_rebuilds"]}
         srv.close()
     summary = {"workload": f"{len(scs)} drop impacts of seeded sides {min(sc.shape[0] for _, sc in scs)}.."
@@ -629,7 +664,9 @@ def bench_serve(args, emit=True):
                            f"{steps} steps each, D3Q19 TRT OM, replayed in real time",
                "cells": cells, "unit": "MLUPS", "results": out, "max_active": args.max_active,
                "chunk_steps": args.chunk_steps,
-               "observable": "crown height max over interface cells of (k + fill), relative to the plain FP32 run"}
+               "observable": "crown height max over interface cells of (k + fill), and the liquid volume above "
+                             "the pool (sum of the fill level over layers k >= depth + 2), each relative to the "
+                             "plain FP32 run"}
     if emit:
         print(json.dumps({"metric": METRIC, "workload": "served drop impacts (continuous batching)", **summary,
                           "data": "synthetic (seeded generator, no dataset)"}), flush=True)

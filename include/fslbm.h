@@ -194,6 +194,29 @@ fslbm_status fslbm_sync(fslbm_ctx* ctx);
  * *out filled) when max |u| >= c_s or a NaN was seen. */
 fslbm_status fslbm_observables(fslbm_ctx* ctx, fslbm_obs* out);
 
+/* Liquid-front radius statistics of one z-layer. */
+typedef struct {
+  int64_t count;   /* front cells                                        */
+  double r_min, r_max, r_mean; /* radius of their cell centres about the
+                                  centre; 0 when count is 0              */
+} fslbm_front_stats;
+
+/* Seed-fill front detection (Sec. 4.3, cylindrical dam break: the front
+ * radius is taken over the interface cells that a seed fill started at a
+ * domain boundary reaches, i.e. the outermost ones).  In the z-layer
+ * `layer`, the fill runs through the cells that are gas or obstacle, over
+ * in-plane face neighbours (across periodic x/y faces too), seeded with
+ * every such cell on the layer's edge (x = 0, nx-1 or y = 0, ny-1).  A front
+ * cell is an interface cell of the layer with a reached gas cell among its
+ * in-plane face neighbours; its radius is the distance of its centre
+ * (x + 1/2, y + 1/2) to (xc, yc).  front_mask (optional, host, nx*ny bytes,
+ * index x + nx*y) receives 1 for front cells.  Synchronizes.  FSLBM_EINVAL
+ * for a layer outside [0, nz) or a non-finite centre; FSLBM_ESTATE before
+ * init.  r_mean sums the radii with device atomics (order not fixed); the
+ * count, mask, r_min and r_max do not depend on the order. */
+fslbm_status fslbm_front(fslbm_ctx* ctx, int layer, double xc, double yc, fslbm_front_stats* out,
+                         uint8_t* front_mask);
+
 /* Copy fields to host buffers (any pointer may be NULL); synchronizes.
  * pdf[q*N] direction-major post-collision PDFs as FP64, fill[N], flags[N]
  * (0..3), mass[N] (meaningful on interface cells; 0 on gas). */

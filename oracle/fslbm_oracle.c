@@ -87,6 +87,15 @@
  *       cell runs over these wall links like over lattice links, so the
  *       masses of interface cells keep track of the PDFs that move between
  *       cells along a wall.
+ *   R23 seed-fill front (Sec. 4.3, cylindrical dam break: the front radius
+ *       is taken over the interface cells that a seed fill started at a
+ *       domain boundary reaches): the fill runs in one z-layer, through the
+ *       cells that are gas or obstacle, over in-plane face neighbours
+ *       (across periodic faces too), seeded with every such cell on the
+ *       layer's edge (x = 0, nx-1 or y = 0, ny-1).  A front cell is an
+ *       interface cell of the layer with a reached gas cell among its
+ *       in-plane face neighbours.  Its radius is the distance of its cell
+ *       centre (x + 1/2, y + 1/2) to the given centre (xc, yc).
  *
  * R8 has one exception: a gas cell that becomes interface gets f^eq of the
  * mean density and velocity of its neighbours (R14), with no collision, so
@@ -1151,3 +1160,94 @@ double orc_total_mass(const orc* o) {
   }
   return M + comp;
 }
+
+/* Seed-fill front detection (R23) on the layer z = layer of a flags array
+ * (caller order c = x + nx (y + ny z)).  front[nx*ny] (optional) receives 1
+ * for front cells; stats[4] = count, minimum, maximum and mean radius
+ * (0 when no front cell).  A plain breadth-first fill with a queue. */
+int orc_seed_fill_front(int nx, int ny, int nz, int per_x, int per_y, const unsigned char* flags,
+                        int layer, double xc, double yc, unsigned char* front, double* stats) {
+  long M, c, head = 0, tail = 0;
+  int x, y, k;
+  unsigned char* reach;
+  long* queue;
+  const unsigned char* fl;
+  double n = 0.0, rmin = 0.0, rmax = 0.0, rsum = 0.0;
+  if (nx < 1 || ny < 1 || nz < 1 || layer < 0 || layer >= nz || !flags || !stats) return 1;
+  M = (long)nx * ny;
+  fl = flags + (long)layer * M;
+  reach = (unsigned char*)calloc((size_t)M, 1);
+  queue = (long*)malloc(sizeof(long) * (size_t)M);
+  if (!reach || !queue) {
+    free(reach);
+    free(queue);
+    return 1;
+  }
+  /* seeds: gas or obstacle cells on the layer's edge */
+  for (y = 0; y < ny; ++y)
+    for (x = 0; x < nx; ++x) {
+      c = x + (long)nx * y;
+      if ((x == 0 || x == nx - 1 || y == 0 || y == ny - 1) && (fl[c] == GAS || fl[c] == OBST)) {
+        reach[c] = 1;
+        queue[tail++] = c;
+      }
+    }
+  while (head < tail) {
+    const long cur = queue[head++];
+    const int cx = (int)(cur % nx), cy = (int)(cur / nx);
+    for (k = 0; k < 4; ++k) {
+      int X = cx + (k == 0) - (k == 1), Y = cy + (k == 2) - (k == 3);
+      long nb;
+      if (X < 0 || X >= nx) {
+        if (!per_x) continue;
+        X = (X + nx) % nx;
+      }
+      if (Y < 0 || Y >= ny) {
+        if (!per_y) continue;
+        Y = (Y + ny) % ny;
+      }
+      nb = X + (long)nx * Y;
+      if (!reach[nb] && (fl[nb] == GAS || fl[nb] == OBST)) {
+        reach[nb] = 1;
+        queue[tail++] = nb;
+      }
+    }
+  }
+  for (y = 0; y < ny; ++y)
+    for (x = 0; x < nx; ++x) {
+      int hit = 0;
+      c = x + (long)nx * y;
+      if (fl[c] == IFACE)
+        for (k = 0; k < 4; ++k) {
+          int X = x + (k == 0) - (k == 1), Y = y + (k == 2) - (k == 3);
+          long nb;
+          if (X < 0 || X >= nx) {
+            if (!per_x) continue;
+            X = (X + nx) % nx;
+          }
+          if (Y < 0 || Y >= ny) {
+            if (!per_y) continue;
+            Y = (Y + ny) % ny;
+          }
+          nb = X + (long)nx * Y;
+          if (reach[nb] && fl[nb] == GAS) hit = 1;
+        }
+      if (front) front[c] = (unsigned char)hit;
+      if (hit) {
+        const double dx = (x + 0.5) - xc, dy = (y + 0.5) - yc;
+        const double r = sqrt(dx * dx + dy * dy);
+        if (n == 0.0 || r < rmin) rmin = r;
+        if (n == 0.0 || r > rmax) rmax = r;
+        rsum += r;
+        n += 1.0;
+      }
+    }
+  stats[0] = n;
+  stats[1] = rmin;
+  stats[2] = rmax;
+  stats[3] = n > 0.0 ? rsum / n : 0.0;
+  free(reach);
+  free(queue);
+  return 0;
+}
+

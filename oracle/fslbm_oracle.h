@@ -82,6 +82,13 @@ void orc_reconstruct(int q, const int* recon, double rho_g, const double* u,
 double orc_k8_smooth(const double* block27);
 void orc_py_gradient(const double* block27, double* n3);
 
+/* ---- observables on a flags array (caller order x + nx (y + ny z)) ---- */
+/* Seed-fill front of the layer z = layer (reading R23): front[nx*ny]
+ * (optional) gets 1 for front cells; stats[4] = count, min, max and mean of
+ * their radius about (xc, yc).  Returns 0, or 1 on bad arguments. */
+int orc_seed_fill_front(int nx, int ny, int nz, int per_x, int per_y, const unsigned char* flags,
+                        int layer, double xc, double yc, unsigned char* front, double* stats);
+
 #ifdef __cplusplus
 }
 #endif

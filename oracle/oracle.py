@@ -80,6 +80,9 @@ def _load(openmp: bool = False):
         lib.orc_k8_smooth.restype = d
         lib.orc_k8_smooth.argtypes = [p]
         lib.orc_py_gradient.argtypes = [p, p]
+        lib.orc_seed_fill_front.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, p, C.c_int,
+                                            C.c_double, C.c_double, p, p]
+        lib.orc_seed_fill_front.restype = C.c_int
         if openmp:
             _lib_omp = lib
         else:
@@ -158,6 +161,24 @@ def py_gradient(block) -> np.ndarray:
     out = np.zeros(3, np.float64)
     lib.orc_py_gradient(_ptr(b), _ptr(out))
     return out
+
+
+def seed_fill_front(flags, shape, layer, center, periodic=(False, False)):
+    """Seed-fill front of the z-layer ``layer`` of a flags array in caller
+    order (reading R23): returns (front mask [ny, nx] of bools, dict with
+    count, r_min, r_max, r_mean about ``center`` = (xc, yc))."""
+    lib = _load()
+    nx, ny, nz = shape
+    fl = np.ascontiguousarray(flags, np.uint8).reshape(-1)
+    assert fl.size == nx * ny * nz
+    front = np.zeros(nx * ny, np.uint8)
+    st = np.zeros(4, np.float64)
+    rc = lib.orc_seed_fill_front(nx, ny, nz, int(bool(periodic[0])), int(bool(periodic[1])), _ptr(fl),
+                                 int(layer), float(center[0]), float(center[1]), _ptr(front), _ptr(st))
+    if rc != 0:
+        raise ValueError("bad arguments")
+    return front.reshape(ny, nx).astype(bool), {"count": int(st[0]), "r_min": st[1], "r_max": st[2],
+                                                "r_mean": st[3]}
 
 
 class Oracle:

@@ -2,7 +2,7 @@
 
 Each translation unit under ``csrc/`` is compiled by its own nvcc process (in
 parallel), and every engine (storage format and lattice) is an object of its
-own; the FP64 engines are compiled with ``--fmad=false`` so their arithmetic
+own; the engines are compiled with ``--fmad=false`` so their arithmetic
 rounds exactly as written.  The shared library links the CUDA runtime
 dynamically so that it shares one runtime with PyTorch in the same process.
 """
@@ -20,17 +20,20 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfslbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, object, flags): the C-ABI units, then one engine per storage
-# format and lattice from fslbm_engine_inst.cu (the FP64 engine without
-# multiply-add contraction, so that it rounds exactly as written)
+# format and lattice from fslbm_engine_inst.cu, all without multiply-add
+# contraction: the FP64 engine then rounds exactly as written (bitwise the
+# oracle), and in every engine a cell's arithmetic is the same in each
+# kernel that inlines it (single-domain and batched runs agree bitwise);
+# the hot FP32 collision writes its multiply-adds out as fused operations
 ENGINES = [("f64", "StoreF64"), ("f32", "StoreF32"), ("f16s", "StoreF16S"), ("bf16s", "StoreBF16S"),
            ("f32mc", "StoreF32MC"), ("f16smc", "StoreF16SMC")]
 SOURCES = [(f, f.replace(".cu", ".o"), []) for f in
-           ("fslbm_api.cu", "fslbm_noalloc.cu", "fslbm_batch.cu", "fslbm_server.cu")]
+           ("fslbm_api.cu", "fslbm_noalloc.cu", "fslbm_batch.cu", "fslbm_server.cu", "fslbm_front.cu")]
 for _name, _store in ENGINES:
     for _q in (19, 27):
         SOURCES.append(("fslbm_engine_inst.cu", f"engine_{_name}_q{_q}.o",
                         [f"-DFSLBM_INST_NAME=ops_{_name}_q{_q}", f"-DFSLBM_INST_Q={_q}",
-                         f"-DFSLBM_INST_STORE={_store}"] + (["--fmad=false"] if _name == "f64" else [])))
+                         f"-DFSLBM_INST_STORE={_store}", "--fmad=false"]))
 
 
 def nvcc() -> str:

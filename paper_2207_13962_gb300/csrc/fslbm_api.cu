@@ -121,7 +121,7 @@ cudaError_t build_graphs(fslbm_ctx* c) {
 }
 
 int launches_per_step(const fslbm_ctx* c) {
-  return 7 + ((c->kp.bubble_model && c->d.nb > 0) ? 1 : 0);
+  return c->ops.step_launches + ((c->kp.bubble_model && c->d.nb > 0) ? 1 : 0);
 }
 
 

@@ -33,9 +33,6 @@ struct fslbm_batch {
 
 namespace {
 
-// kernels of one batched step: two plan kernels, geometry, bulk sweep,
-// interface update, resolve, count, apply, finalize, bubbles + buffer swap
-constexpr int kBatchLaunchesPerStep = 10;
 
 fslbm_status bfail(fslbm_batch* b, fslbm_status s, const std::string& msg) {
   if (b) b->err = msg;
@@ -101,7 +98,7 @@ cudaError_t launch(fslbm_batch* b, int n) {
       c->parity ^= (n & 1);
       c->step += n;
     }
-    b->launches += (long long)n * kBatchLaunchesPerStep;
+    b->launches += (long long)n * b->ops.batch_step_launches;
   }
   return e;
 }
@@ -139,8 +136,9 @@ fslbm_status fslbm_batch_create(fslbm_ctx* const* members, int n, void* stream, 
   b->tune.band_blocks_per_sm = 2;
   b->tune.ms_per_step = 0.0;
   cudaError_t e = cudaMalloc(&b->d_recs, (size_t)n * sizeof(DomRec));
-  // four prefix arrays of n + 1 entries, then the bulk sweep's hand-out counter
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_off, (4 * (size_t)(n + 1) + 1) * sizeof(int));
+  // four prefix arrays of n + 1 entries, then the bulk sweep's hand-out
+  // counter and the fused sweep's tile counter
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_off, (4 * (size_t)(n + 1) + 2) * sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->fork.side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.fork, cudaEventDisableTiming);

@@ -123,9 +123,9 @@ constexpr int bulk_min_blocks() {
   return sizeof(typename S::Real) == 4 ? (coll_les(COLL) ? 3 : kBulkMinBlocks32) : 2;
 }
 
+// The sweep over the liquid segments by the warps of a persistent grid.
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
-    k_bulk(DPtrs d, KParams p, int parity) {
+__device__ __forceinline__ void bulk_sweep(const DPtrs& d, const KParams& p, int parity) {
   constexpr int kGroups = 32 / kSegCells;
   const int nseg = d.counts[5];
   if constexpr (kBulkChunk > 0) {
@@ -143,6 +143,12 @@ __global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
     for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w * kGroups < nseg; w += warps)
       bulk_unit<Q, S, COLL>(d, p, parity, w, nseg);
   }
+}
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
+    k_bulk(DPtrs d, KParams p, int parity) {
+  bulk_sweep<Q, S, COLL>(d, p, parity);
 }
 
 }  // namespace fslbm

@@ -267,16 +267,21 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
     if (CY(i) != 0) jy += float(CY(i)) * d[i];
     if (CZ(i) != 0) jz += float(CZ(i)) * d[i];
   }
+  // The engines are compiled without multiply-add contraction (so that a
+  // cell's arithmetic does not depend on the kernel it is inlined into); the
+  // multiply-adds of this hot loop are written out as fused operations.
   const float rho = 1.0f + dr;
   const float gx = p.fg[0], gy = p.fg[1], gz = p.fg[2];
   const float inv = __frcp_rn(rho);
-  const float ux = jx * inv + 0.5f * gx, uy = jy * inv + 0.5f * gy, uz = jz * inv + 0.5f * gz;
+  const float ux = __fmaf_rn(jx, inv, 0.5f * gx), uy = __fmaf_rn(jy, inv, 0.5f * gy),
+              uz = __fmaf_rn(jz, inv, 0.5f * gz);
   const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
-  const float usq = ux * ux + uy * uy + uz * uz;
+  const float usq = __fmaf_rn(ux, ux, __fmaf_rn(uy, uy, uz * uz));
   if (!(usq < 1.0f / 3.0f) || !(rho > 0.f)) unstable = true;
   float omp = p.fomega, prp = p.fpref_p;
   float omm = coll_trt(COLL) ? p.fom_m : omp, prm = coll_trt(COLL) ? p.fpref_m : prp;
-  const float base = dr - 1.5f * rho * usq;
+  const float base = __fmaf_rn(-1.5f * rho, usq, dr);
+  const float r45 = 4.5f * rho;
   if constexpr (coll_les(COLL)) {
     // momentum flux of the non-equilibrium part: the pair (i, ibar) shares
     // c_a c_b, and d_i - e_i + d_ibar - e_ibar = d_i + d_ibar - 2 es (the
@@ -286,8 +291,8 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
     for (int i = 1; i < Q; i += 2) {
       const float cx = float(CX(i)), cy = float(CY(i)), cz = float(CZ(i));
       const float cu = cx * ux + cy * uy + cz * uz;
-      const float es = W<Q, float>(i) * (base + 4.5f * rho * cu * cu);
-      const float dn = d[i] + d[i + 1] - 2.0f * es;
+      const float es = W<Q, float>(i) * __fmaf_rn(r45 * cu, cu, base);
+      const float dn = __fmaf_rn(-2.0f, es, d[i] + d[i + 1]);
       qxx += cx * cx * dn;
       qyy += cy * cy * dn;
       qzz += cz * cz * dn;
@@ -305,10 +310,11 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
       prm = prp;
     }
   }
-  const float uF3 = 3.0f * (ux * Fx + uy * Fy + uz * Fz);
+  const float uF3 = 3.0f * __fmaf_rn(ux, Fx, __fmaf_rn(uy, Fy, uz * Fz));
   {
     const float w = W<Q, float>(0);
-    d[0] = d[0] - omp * (d[0] - w * base) - prp * w * uF3;
+    const float t0 = __fmaf_rn(-w, base, d[0]);  // d_0 - w base
+    d[0] = __fmaf_rn(-omp, t0, __fmaf_rn(-prp * w, uF3, d[0]));
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -316,14 +322,14 @@ __device__ __forceinline__ float collide_dev(float* d, const KParams& p, bool& u
     const float w = W<Q, float>(i);
     const float cu = float(CX(i)) * ux + float(CY(i)) * uy + float(CZ(i)) * uz;
     const float cF = float(CX(i)) * Fx + float(CY(i)) * Fy + float(CZ(i)) * Fz;
-    const float es = w * (base + 4.5f * rho * cu * cu);
-    const float ea = 3.0f * w * rho * cu;
-    const float ss = w * (9.0f * cu * cF - uF3);
-    const float sa = 3.0f * w * cF;
+    const float es = w * __fmaf_rn(r45 * cu, cu, base);
+    const float ea = (3.0f * w) * rho * cu;
+    const float ss = w * __fmaf_rn(9.0f * cu, cF, -uF3);
+    const float sa = (3.0f * w) * cF;
     const float fp = 0.5f * (d[i] + d[j]);
     const float fm = 0.5f * (d[i] - d[j]);
-    const float A = omp * (fp - es) - prp * ss;
-    const float B = omm * (fm - ea) - prm * sa;
+    const float A = __fmaf_rn(omp, fp - es, -prp * ss);
+    const float B = __fmaf_rn(omm, fm - ea, -prm * sa);
     const float di = d[i] - A - B;
     const float dj = d[j] - A + B;
     d[i] = di;

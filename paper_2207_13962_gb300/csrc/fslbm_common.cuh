@@ -320,6 +320,54 @@ __device__ __forceinline__ R gpar(const KParams& p, int a) {
   else return p.g[a];
 }
 
+// FP64 arithmetic and conversions run on this GPU's small FP64 unit (two
+// lanes a clock per SM), so the FP32 engines keep it out of per-neighbour
+// work with the two helpers below.
+
+// x rounded to the nearest float (ties to even) with integer operations.
+// Magnitudes below 2^-126 give a signed zero (the fill levels and masses it
+// converts never come near); infinities and NaN take the conversion
+// instruction.
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  const unsigned sign = hi & 0x80000000u;
+  if (ex == 0x7ffu) return __double2float_rn(x);
+  const int fe = (int)ex - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const unsigned rem = lo & 0x1fffffffu;                    // the 29 dropped bits
+  unsigned r = sign | ((unsigned)fe << 23) | m;
+  // round to nearest, ties to even; a carry out of the mantissa raises the
+  // exponent (to infinity past the largest float)
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) r += 1u;
+  return __uint_as_float(r);
+}
+
+// A sum of floats held as an unevaluated pair hi + lo: each addition's
+// rounding error (Knuth's TwoSum, exact in round-to-nearest) goes to lo, so
+// the pair carries about 48 significant bits.
+struct FAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bv = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  // adds a - b exactly (its rounding error goes to lo as well)
+  __device__ __forceinline__ void add_diff(float a, float b) {
+    const float s = __fsub_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fadd_rn(b, bv));
+    add(s);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Device pointers of one domain.
 struct DPtrs {
   void* pdf[2];
@@ -340,7 +388,8 @@ struct DPtrs {
   double* share;
   int* band[2];
   int* counts;   // [0],[1]: band list counts; [2]: new-cell list count;
-                 // [3],[4]: geometry tile list counts; [5]: segment count
+                 // [3],[4]: geometry tile list counts; [5]: segment count;
+                 // [6], [7]: the step's bulk-unit and tile hand-out
   int* tiles[2]; // geometry tiles (8^3) holding interface cells
   int* tile_mark;
   int* segs;     // 32-cell segments (linear index / 32) holding liquid;

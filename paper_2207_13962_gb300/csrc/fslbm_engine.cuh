@@ -39,6 +39,14 @@ struct Engine {
     return sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2;
   }
   static int grid_cells(const KParams& p) { return (p.N + kBlock - 1) / kBlock; }
+  // the FP32 and 16-bit engines fold the geometry pass into the bulk sweep
+  static constexpr bool kFusedGeo = sizeof(typename S::Real) == 4 && !kTmaBulk;
+  // shared-memory carveout (percent of the 228 KB) that holds a tile buffer
+  // for every persistent block of the fused sweep; the rest stays L1
+  static constexpr int fused_carveout() {
+    return (kBulkMinBlocks32 * ((int)geometry_smem<typename S::Real>() + 1024) * 100 + 228 * 1024 - 1) /
+           (228 * 1024);
+  }
 
   static void init_cells(const DPtrs& d, const KParams& p, const uint8_t* raw, const double* fill,
                          const double* vel, const double* den, cudaStream_t st) {
@@ -63,6 +71,32 @@ struct Engine {
   static void step(const DPtrs& d, const KParams& p, int parity, int band_grid, int bulk_grid,
                    cudaStream_t st, StageEvents* ev, const Fork* fk) {
     const int coll = iface_coll(p);
+    if constexpr (kFusedGeo) {
+      // geometry and bulk in one persistent launch, then the band chain
+      constexpr size_t sm = geometry_smem<typename S::Real>();
+      if (ev) {
+        ev->mark(0, st);
+        ev->mark(1, st);
+      }
+      with_coll(coll, [&](auto C) { k_bulk_geo<Q, S, decltype(C)::value><<<bulk_grid, kBulkBlock, sm, st>>>(d, p, parity); });
+      if (ev) ev->mark(2, st);
+      with_coll(coll, [&](auto C) {
+        k_interface<Q, S, decltype(C)::value><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+      });
+      if (ev) ev->mark(3, st);
+      k_resolve<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+      if (ev) ev->mark(4, st);
+      k_count<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+      if (ev) ev->mark(5, st);
+      k_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+      if (ev) ev->mark(6, st);
+      k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
+      if (ev) ev->mark(7, st);
+      if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
+      if (ev) ev->mark(8, st);
+      (void)fk;
+      return;
+    }
     auto bulk = [&](cudaStream_t s2) {
       with_coll(coll, [&](auto C) {
         constexpr int CO = decltype(C)::value;
@@ -112,6 +146,23 @@ struct Engine {
   static void batch_step(DomRec* recs, const BatchPlan& pl, int band_grid, int bulk_grid,
                          int collision, cudaStream_t st, const Fork* fk) {
     kb_plan_front<<<1, 1024, 0, st>>>(recs, pl);
+    if constexpr (kFusedGeo) {
+      constexpr size_t sm = geometry_smem<typename S::Real>();
+      with_coll(collision, [&](auto C) {
+        kb_bulk_geo<Q, S, decltype(C)::value><<<bulk_grid, kBulkBlock, sm, st>>>(recs, pl);
+      });
+      with_coll(collision, [&](auto C) {
+        kb_interface<Q, S, decltype(C)::value><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+      });
+      kb_resolve<Q><<<band_grid, kBlock, 0, st>>>(recs, pl);
+      kb_count<Q><<<band_grid, kBlock, 0, st>>>(recs, pl);
+      kb_plan_back<<<1, 1024, 0, st>>>(recs, pl);
+      kb_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(recs, pl);
+      kb_finalize<<<band_grid, kBlock, 0, st>>>(recs, pl);
+      kb_bubble_end<<<pl.n, 256, 0, st>>>(recs);
+      (void)fk;
+      return;
+    }
     cudaEventRecord(fk->fork, st);
     cudaStreamWaitEvent(fk->side, fk->fork, 0);
     with_coll(collision, [&](auto C) {
@@ -166,30 +217,57 @@ struct Engine {
     o.elem_size = sizeof(typename S::T);
     o.real_size = sizeof(typename S::Real);
     o.rest_size = S::kExactRest ? sizeof(int) : 0;
-    if constexpr (kTmaBulk) {
-      o.bulk_fn[0] = (const void*)&k_bulk_tma<Q, S, 0>;
-      o.bulk_fn[1] = (const void*)&k_bulk_tma<Q, S, 1>;
+    if constexpr (kFusedGeo) {
+      const void* fns[8] = {(const void*)&k_bulk_geo<Q, S, 0>, (const void*)&k_bulk_geo<Q, S, 1>,
+                            (const void*)&k_bulk_geo<Q, S, 2>, (const void*)&k_bulk_geo<Q, S, 3>,
+                            (const void*)&k_bulk_geo<Q, S, 4>, (const void*)&k_bulk_geo<Q, S, 5>,
+                            (const void*)&k_bulk_geo<Q, S, 6>, (const void*)&k_bulk_geo<Q, S, 7>};
+      for (int c = 0; c < 8; ++c) {
+        o.bulk_fn[c] = fns[c];
+        cudaFuncSetAttribute(fns[c], cudaFuncAttributePreferredSharedMemoryCarveout, fused_carveout());
+      }
     } else {
-      o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
-      o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
+      if constexpr (kTmaBulk) {
+        o.bulk_fn[0] = (const void*)&k_bulk_tma<Q, S, 0>;
+        o.bulk_fn[1] = (const void*)&k_bulk_tma<Q, S, 1>;
+      } else {
+        o.bulk_fn[0] = (const void*)&k_bulk<Q, S, 0>;
+        o.bulk_fn[1] = (const void*)&k_bulk<Q, S, 1>;
+      }
+      o.bulk_fn[2] = (const void*)&k_bulk<Q, S, 2>;
+      o.bulk_fn[3] = (const void*)&k_bulk<Q, S, 3>;
+      o.bulk_fn[4] = (const void*)&k_bulk<Q, S, 4>;
+      o.bulk_fn[5] = (const void*)&k_bulk<Q, S, 5>;
+      o.bulk_fn[6] = (const void*)&k_bulk<Q, S, 6>;
+      o.bulk_fn[7] = (const void*)&k_bulk<Q, S, 7>;
     }
-    o.bulk_fn[2] = (const void*)&k_bulk<Q, S, 2>;
-    o.bulk_fn[3] = (const void*)&k_bulk<Q, S, 3>;
-    o.bulk_fn[4] = (const void*)&k_bulk<Q, S, 4>;
-    o.bulk_fn[5] = (const void*)&k_bulk<Q, S, 5>;
-    o.bulk_fn[6] = (const void*)&k_bulk<Q, S, 6>;
-    o.bulk_fn[7] = (const void*)&k_bulk<Q, S, 7>;
     o.bulk_blocks_per_sm = bulk_blocks_per_sm();
-    o.bulk_smem = kTmaBulk ? tma_smem<Q, typename S::T>() : 0;
+    o.step_launches = kFusedGeo ? 6 : 7;
+    o.bulk_smem = kTmaBulk ? tma_smem<Q, typename S::T>() : kFusedGeo ? geometry_smem<typename S::Real>() : 0;
     o.batch_step = &batch_step;
-    o.batch_bulk_fn[0] = (const void*)&kb_bulk<Q, S, 0>;
-    o.batch_bulk_fn[1] = (const void*)&kb_bulk<Q, S, 1>;
-    o.batch_bulk_fn[2] = (const void*)&kb_bulk<Q, S, 2>;
-    o.batch_bulk_fn[3] = (const void*)&kb_bulk<Q, S, 3>;
-    o.batch_bulk_fn[4] = (const void*)&kb_bulk<Q, S, 4>;
-    o.batch_bulk_fn[5] = (const void*)&kb_bulk<Q, S, 5>;
-    o.batch_bulk_fn[6] = (const void*)&kb_bulk<Q, S, 6>;
-    o.batch_bulk_fn[7] = (const void*)&kb_bulk<Q, S, 7>;
+    // two plan kernels, geometry, bulk sweep, interface update, resolve,
+    // count, apply, finalize, bubbles + buffer swap (one less when the
+    // geometry is folded into the sweep)
+    o.batch_step_launches = kFusedGeo ? 9 : 10;
+    if constexpr (kFusedGeo) {
+      const void* fns[8] = {(const void*)&kb_bulk_geo<Q, S, 0>, (const void*)&kb_bulk_geo<Q, S, 1>,
+                            (const void*)&kb_bulk_geo<Q, S, 2>, (const void*)&kb_bulk_geo<Q, S, 3>,
+                            (const void*)&kb_bulk_geo<Q, S, 4>, (const void*)&kb_bulk_geo<Q, S, 5>,
+                            (const void*)&kb_bulk_geo<Q, S, 6>, (const void*)&kb_bulk_geo<Q, S, 7>};
+      for (int c = 0; c < 8; ++c) {
+        o.batch_bulk_fn[c] = fns[c];
+        cudaFuncSetAttribute(fns[c], cudaFuncAttributePreferredSharedMemoryCarveout, fused_carveout());
+      }
+    } else {
+      o.batch_bulk_fn[0] = (const void*)&kb_bulk<Q, S, 0>;
+      o.batch_bulk_fn[1] = (const void*)&kb_bulk<Q, S, 1>;
+      o.batch_bulk_fn[2] = (const void*)&kb_bulk<Q, S, 2>;
+      o.batch_bulk_fn[3] = (const void*)&kb_bulk<Q, S, 3>;
+      o.batch_bulk_fn[4] = (const void*)&kb_bulk<Q, S, 4>;
+      o.batch_bulk_fn[5] = (const void*)&kb_bulk<Q, S, 5>;
+      o.batch_bulk_fn[6] = (const void*)&kb_bulk<Q, S, 6>;
+      o.batch_bulk_fn[7] = (const void*)&kb_bulk<Q, S, 7>;
+    }
     return o;
   }
 };

@@ -45,10 +45,12 @@ struct Ops {
                            // every other kernel get the higher priority
   int bulk_blocks_per_sm;  // resident blocks per SM of the persistent bulk sweep
   size_t bulk_smem;        // its dynamic shared memory per block
+  int step_launches;       // kernels one step launches (without the bubble kernel)
   // one step of every domain of a block table (see DomRec, BatchPlan)
   void (*batch_step)(DomRec* recs, const BatchPlan& plan, int band_grid, int bulk_grid,
                      int collision, cudaStream_t, const Fork*);
   const void* batch_bulk_fn[8];
+  int batch_step_launches;  // kernels one batched step launches
 };
 
 // Collision variant of a parameter block: bit 0 TRT (else SRT), bit 1 the

@@ -23,6 +23,7 @@
 #pragma once
 
 #include "fslbm_bulk_tma.cuh"
+#include <type_traits>
 
 namespace fslbm {
 
@@ -312,15 +313,18 @@ __device__ __forceinline__ R k8w(int n2) {
 // phi~ (K8 smoothing, radius 2) is formed on the 12^3 sub-box, n^ (Parker-
 // Youngs, Eq. nm-fslbm-normal) on the 10^3 sub-box and kappa = -div(n^) on
 // the interface cells of the tile.  Obstacle and out-of-domain stencil
-// points take the stencil centre's value.  Each value uses the same
-// arithmetic and summation order as a per-cell evaluation.
+// points take the stencil centre's value.  In the FP64 engine each value
+// uses the same arithmetic and summation order as a per-cell evaluation.
 constexpr int GT = 8;                    // tile edge
 constexpr int GE = GT + 6;               // box edge with halo 3
 constexpr int GB = GE * GE * GE;         // 2744 box positions
 constexpr int GS = GT + 4;               // phi~ sub-box edge (12)
 constexpr int GN = GT + 2;               // n^ sub-box edge (10)
 constexpr int kGeoBlock = 192;  // the z-column phases use 144 and 100 threads
-constexpr int kGeoPer = (GB + kGeoBlock - 1) / kGeoBlock;  // box positions per thread
+#ifndef FSLBM_GEO_LOAD_BATCH
+#define FSLBM_GEO_LOAD_BATCH 6
+#endif
+constexpr int kGeoLoadBatch = FSLBM_GEO_LOAD_BATCH;  // box positions a thread loads at once
 // geometry blocks per interface-band block: each tile's block runs four
 // dependent shared-memory phases, so many resident tiles hide the latency
 #ifndef FSLBM_GEO_MULT
@@ -339,20 +343,25 @@ __device__ __forceinline__ R kObstacle() { return R(-1.0e30); }
 template <class R>
 __device__ __forceinline__ bool is_obstacle(R v) { return v < R(-1.0e29); }
 
+// Shared memory of one tile: the fill-level box, whose space the normals
+// take over once the smoothing has read it, the smoothed sub-box and the
+// types.
+constexpr int kGeoBoxSlots = GB > 3 * GN * GN * GN ? GB : 3 * GN * GN * GN;
 template <class R>
 constexpr size_t geometry_smem() {
-  return sizeof(R) * (GB + GS * GS * GS + 3 * GN * GN * GN) + GB;
+  return sizeof(R) * (kGeoBoxSlots + GS * GS * GS) + GB;
 }
 
-// One 8^3 tile of the geometry pass (every thread of the block calls it).
-template <int Q, class S>
+// One 8^3 tile of the geometry pass (all NT threads of the block call it).
+template <int Q, class S, int NT = kGeoBlock>
 __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, int tile,
                                               unsigned char* g_smem) {
   using R = typename S::Real;
+  constexpr int kPer = (GB + NT - 1) / NT;  // box positions per thread
   R* sphi = (R*)g_smem;
-  R* sps = sphi + GB;
-  R* snh = sps + GS * GS * GS;
-  uint8_t* styp = (uint8_t*)(snh + 3 * GN * GN * GN);
+  R* snh = sphi;  // written after the smoothing's last read of sphi
+  R* sps = sphi + kGeoBoxSlots;
+  uint8_t* styp = (uint8_t*)(sps + GS * GS * GS);
   const int ntx = (p.nx + GT - 1) / GT, nty = (p.ny + GT - 1) / GT;
   R* nhat = (R*)d.nhat;
   R* rhog = (R*)d.rhog;
@@ -361,9 +370,9 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
     const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const int ox = tx * GT - 3, oy = ty * GT - 3, oz = tz * GT - 3;
     // all of a thread's global reads of the box are issued before the first
-    // shared-memory store (kGeoBlock threads, kGeoPer positions each)
+    // shared-memory store (NT threads, kPer positions each)
     __syncthreads();
-    // Thread t loads box position t + r kGeoBlock counted in the cells'
+    // Thread t loads box position t + r NT counted in the cells'
     // storage order (its first coordinate runs along the contiguous axis),
     // so that the loads of a warp coalesce whatever the storage order; the
     // shared-memory box itself is indexed in the caller's axes.
@@ -373,123 +382,256 @@ __device__ __forceinline__ void geometry_tile(const DPtrs& d, const KParams& p, 
       j = sel3(p.inv[1], k0, k1, k2);
       k = sel3(p.inv[2], k0, k1, k2);
     };
-    uint8_t tv[kGeoPer];
-    R pv[kGeoPer];
+    // in kLoadRounds rounds of at most kBatch positions, so that the loads in
+    // flight fit the registers of a 64-register thread
+    constexpr int kBatch = kGeoLoadBatch < kPer ? kGeoLoadBatch : kPer;
+    bool solid_here = false;  // an obstacle or a position outside the domain
 #pragma unroll
-    for (int r = 0; r < kGeoPer; ++r) {
-      const int b = threadIdx.x + r * kGeoBlock;
-      tv[r] = 4;  // outside the domain: solid
-      pv[r] = R(0.0);
-      if (b < GB) {
-        int i, j, k;
-        box_pos(b, i, j, k);
-        const int X = wrapc(ox + i, p.nx, p.per[0]);
-        const int Y = wrapc(oy + j, p.ny, p.per[1]);
-        const int Z = wrapc(oz + k, p.nz, p.per[2]);
-        if (X >= 0 && Y >= 0 && Z >= 0) {
-          const int c = cidx(p, X, Y, Z);
-          tv[r] = d.flags[c] & F_TYPE;
-          pv[r] = R(d.phi[c]);
+    for (int r0 = 0; r0 < kPer; r0 += kBatch) {
+      uint8_t tv[kBatch];
+      R pv[kBatch];
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const int b = threadIdx.x + (r0 + q) * NT;
+        tv[q] = 4;  // outside the domain: solid
+        pv[q] = R(0.0);
+        if (r0 + q < kPer && b < GB) {
+          int i, j, k;
+          box_pos(b, i, j, k);
+          const int X = wrapc(ox + i, p.nx, p.per[0]);
+          const int Y = wrapc(oy + j, p.ny, p.per[1]);
+          const int Z = wrapc(oz + k, p.nz, p.per[2]);
+          if (X >= 0 && Y >= 0 && Z >= 0) {
+            const int c = cidx(p, X, Y, Z);
+            tv[q] = d.flags[c] & F_TYPE;
+            if constexpr (sizeof(R) == 4) pv[q] = d2f(d.phi[c]);
+            else pv[q] = d.phi[c];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kBatch; ++q) {
+        const int b = threadIdx.x + (r0 + q) * NT;
+        if (r0 + q < kPer && b < GB) {
+          int i, j, k;
+          box_pos(b, i, j, k);
+          const int bs = i + GE * (j + GE * k);
+          styp[bs] = tv[q];
+          sphi[bs] = tv[q] >= T_OBST ? kObstacle<R>() : pv[q];
+          solid_here |= tv[q] >= T_OBST;
         }
       }
     }
+    // without an obstacle in the box the stencils below need no
+    // substitution (most tiles)
+    const bool solid = __syncthreads_or(solid_here) != 0;
+    // The FP32 engines evaluate the same stencils grouped by z-plane.  The K8
+    // weights depend on r^2 only, so a plane contributes its centre, the sum
+    // of its 4 in-plane face neighbours and of its 4 in-plane corners; the
+    // Parker-Youngs weights (2-|d|)(2-|d'|) factor into [1 2 1] x [1 2 1] x
+    // [-1 0 1].  An obstacle point takes the value of the stencil's centre,
+    // which is the same for every plane of the window, so a plane keeps the
+    // sum over its other points and, beside it, the (weighted) count of its
+    // obstacle points, which multiplies the centre value at the end.  Each
+    // plane's sums are formed once and slide along z (other rounding than a
+    // per-cell evaluation, a fraction of its operations and registers).
+    auto planes32 = [&](auto SOLID) {
+      constexpr bool kSolid = decltype(SOLID)::value;
+      auto nz = [&](R v) { return (kSolid && is_obstacle(v)) ? R(0.0) : v; };
+      auto ob = [&](R v) { return (kSolid && is_obstacle(v)) ? R(1.0) : R(0.0); };
+      if (threadIdx.x < GS * GS) {
+        const int i = threadIdx.x % GS + 1, j = threadIdx.x / GS + 1;
+        // centre, face sum, corner sum and their obstacle counts
+        auto plane = [&](int kk, R& c0, R& f4, R& c4, R& nf, R& nc) {
+          const R* q = sphi + i + GE * (j + GE * kk);
+          c0 = q[0];
+          const R a = q[-1], b = q[1], c = q[-GE], e = q[GE];
+          const R u = q[-GE - 1], v = q[-GE + 1], w = q[GE - 1], x = q[GE + 1];
+          f4 = (nz(a) + nz(b)) + (nz(c) + nz(e));
+          c4 = (nz(u) + nz(v)) + (nz(w) + nz(x));
+          if constexpr (kSolid) {
+            nf = (ob(a) + ob(b)) + (ob(c) + ob(e));
+            nc = (ob(u) + ob(v)) + (ob(w) + ob(x));
+          }
+        };
+        R cm, fm, km, nfm = R(0.0), ncm = R(0.0);
+        R c0, f0, k0, nf0 = R(0.0), nc0 = R(0.0);
+        R cp, fp, kp, nfp = R(0.0), ncp = R(0.0);
+        plane(0, cm, fm, km, nfm, ncm);
+        plane(1, c0, f0, k0, nf0, nc0);
+        const R inv = R(1.0) / wsum;
 #pragma unroll
-    for (int r = 0; r < kGeoPer; ++r) {
-      const int b = threadIdx.x + r * kGeoBlock;
-      if (b < GB) {
-        int i, j, k;
-        box_pos(b, i, j, k);
-        const int bs = i + GE * (j + GE * k);
-        styp[bs] = tv[r];
-        sphi[bs] = tv[r] >= T_OBST ? kObstacle<R>() : pv[r];
+        for (int k = 1; k <= GS; ++k) {
+          plane(k + 1, cp, fp, kp, nfp, ncp);
+          R out;
+          if (kSolid && is_obstacle(c0)) {
+            out = kObstacle<R>();
+          } else {
+            const R pc = c0;
+            const R zm = (kSolid && is_obstacle(cm)) ? pc : cm, zp = (kSolid && is_obstacle(cp)) ? pc : cp;
+            R s1 = (f0 + zm) + zp, s2 = (k0 + fm) + fp, s3 = km + kp;
+            if constexpr (kSolid) {
+              s1 = s1 + nf0 * pc;
+              s2 = s2 + (nc0 + nfm + nfp) * pc;
+              s3 = s3 + (ncm + ncp) * pc;
+            }
+            out = (pc + k8w<R>(1) * s1 + k8w<R>(2) * s2 + k8w<R>(3) * s3) * inv;
+          }
+          sps[(i - 1) + GS * ((j - 1) + GS * (k - 1))] = out;
+          cm = c0; fm = f0; km = k0; nfm = nf0; ncm = nc0;
+          c0 = cp; f0 = fp; k0 = kp; nf0 = nfp; nc0 = ncp;
+        }
       }
-    }
-    __syncthreads();
-    // smoothed fill level on the 12^3 sub-box: one thread per z-column,
-    // the 3x3x3 window slides along z in registers
-    if (threadIdx.x < GS * GS) {
-      const int i = threadIdx.x % GS + 1, j = threadIdx.x / GS + 1;
-      R w[3][9];  // planes k-1, k, k+1 of the window, (dy, dx) row-major
+      __syncthreads();
+      if (threadIdx.x < GN * GN) {
+        const int i = threadIdx.x % GN + 2, j = threadIdx.x / GN + 2;
+        // per plane: gx = S_y D_x psi, gy = S_x D_y psi, s = S_x S_y psi over
+        // the points that are not obstacles, and the same weights summed
+        // over the obstacle points (gxo, gyo, so)
+        auto plane = [&](int kk, R& ctr, R& gx, R& gy, R& sm, R& gxo, R& gyo, R& so) {
+          const R* q = sps + (i - 1) + GS * ((j - 1) + GS * (kk - 1));
+          const R a00 = q[-GS - 1], a01 = q[-GS], a02 = q[-GS + 1];
+          const R a10 = q[-1], a11 = q[0], a12 = q[1];
+          const R a20 = q[GS - 1], a21 = q[GS], a22 = q[GS + 1];
+          ctr = a11;
+          gx = (nz(a02) - nz(a00)) + R(2.0) * (nz(a12) - nz(a10)) + (nz(a22) - nz(a20));
+          gy = (nz(a20) - nz(a00)) + R(2.0) * (nz(a21) - nz(a01)) + (nz(a22) - nz(a02));
+          sm = (nz(a00) + R(2.0) * nz(a01) + nz(a02)) + R(2.0) * (nz(a10) + R(2.0) * nz(a11) + nz(a12)) +
+               (nz(a20) + R(2.0) * nz(a21) + nz(a22));
+          if constexpr (kSolid) {
+            gxo = (ob(a02) - ob(a00)) + R(2.0) * (ob(a12) - ob(a10)) + (ob(a22) - ob(a20));
+            gyo = (ob(a20) - ob(a00)) + R(2.0) * (ob(a21) - ob(a01)) + (ob(a22) - ob(a02));
+            so = (ob(a00) + R(2.0) * ob(a01) + ob(a02)) + R(2.0) * (ob(a10) + R(2.0) * ob(a11) + ob(a12)) +
+                 (ob(a20) + R(2.0) * ob(a21) + ob(a22));
+          }
+        };
+        R t, xm, ym, sm, xom = R(0.0), yom = R(0.0), som = R(0.0);
+        R c0, x0, y0, s0, xo0 = R(0.0), yo0 = R(0.0), so0 = R(0.0);
+        R cp, xp, yp, sp, xop = R(0.0), yop = R(0.0), sop = R(0.0);
+        plane(1, t, xm, ym, sm, xom, yom, som);
+        plane(2, c0, x0, y0, s0, xo0, yo0, so0);
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int e = 0; e < 9; ++e)
-          w[q + 1][e] = sphi[(i + e % 3 - 1) + GE * ((j + e / 3 - 1) + GE * q)];
-      for (int k = 1; k <= GS; ++k) {
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-          w[0][e] = w[1][e];
-          w[1][e] = w[2][e];
-          w[2][e] = sphi[(i + e % 3 - 1) + GE * ((j + e / 3 - 1) + GE * (k + 1))];
+        for (int k = 2; k < 2 + GN; ++k) {
+          plane(k + 1, cp, xp, yp, sp, xop, yop, sop);
+          R n0 = R(0.0), n1 = R(0.0), n2 = R(0.0);
+          if (!(kSolid && is_obstacle(c0))) {
+            n0 = xm + R(2.0) * x0 + xp;
+            n1 = ym + R(2.0) * y0 + yp;
+            n2 = sp - sm;
+            if constexpr (kSolid) {
+              n0 = n0 + (xom + R(2.0) * xo0 + xop) * c0;
+              n1 = n1 + (yom + R(2.0) * yo0 + yop) * c0;
+              n2 = n2 + (sop - som) * c0;
+            }
+          }
+          const R l2 = n0 * n0 + n1 * n1 + n2 * n2;
+          const R il = l2 > R(0.0) ? rsqrtf(l2) : R(0.0);
+          const int s3 = (i - 2) + GN * ((j - 2) + GN * (k - 2));
+          snh[s3] = n0 * il;
+          snh[GN * GN * GN + s3] = n1 * il;
+          snh[2 * GN * GN * GN + s3] = n2 * il;
+          xm = x0; ym = y0; sm = s0; xom = xo0; yom = yo0; som = so0;
+          c0 = cp; x0 = xp; y0 = yp; s0 = sp; xo0 = xop; yo0 = yop; so0 = sop;
         }
-        const R pc = w[1][4];
-        R out = kObstacle<R>();
-        if (!is_obstacle(pc)) {
-          R acc = R(0.0);
-#pragma unroll
-          for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-              for (int dx = -1; dx <= 1; ++dx) {
-                const R raw = w[dz + 1][(dy + 1) * 3 + dx + 1];
-                const R v = is_obstacle(raw) ? pc : raw;
-                acc = acc + k8w<R>(dx * dx + dy * dy + dz * dz) * v;
-              }
-          out = acc / wsum;
-        }
-        sps[(i - 1) + GS * ((j - 1) + GS * (k - 1))] = out;
       }
-    }
-    __syncthreads();
-    // Parker-Youngs normal on the 10^3 sub-box, z-columns as above
-    if (threadIdx.x < GN * GN) {
-      const int i = threadIdx.x % GN + 2, j = threadIdx.x / GN + 2;
-      auto psi = [&](int ii, int jj, int kk) { return sps[(ii - 1) + GS * ((jj - 1) + GS * (kk - 1))]; };
-      R w[3][9];
+    };
+    auto stencils = [&](auto SOLID) {
+      constexpr bool kSolid = decltype(SOLID)::value;
+      // smoothed fill level on the 12^3 sub-box: one thread per z-column,
+      // the 3x3x3 window slides along z in registers
+      if (threadIdx.x < GS * GS) {
+        const int i = threadIdx.x % GS + 1, j = threadIdx.x / GS + 1;
+        R w[3][9];  // planes k-1, k, k+1 of the window, (dy, dx) row-major
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
-        for (int e = 0; e < 9; ++e) w[q + 1][e] = psi(i + e % 3 - 1, j + e / 3 - 1, 1 + q);
-      for (int k = 2; k < 2 + GN; ++k) {
+          for (int e = 0; e < 9; ++e)
+            w[q + 1][e] = sphi[(i + e % 3 - 1) + GE * ((j + e / 3 - 1) + GE * q)];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) {
-          w[0][e] = w[1][e];
-          w[1][e] = w[2][e];
-          w[2][e] = psi(i + e % 3 - 1, j + e / 3 - 1, k + 1);
-        }
-        auto at = [&](int dx, int dy, int dz) { return w[dz + 1][(dy + 1) * 3 + dx + 1]; };
-        const R pc = at(0, 0, 0);
-        R out[3] = {R(0.0), R(0.0), R(0.0)};
-        if (!is_obstacle(pc)) {
-          R nn[3];
+        for (int k = 1; k <= GS; ++k) {
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
+          for (int e = 0; e < 9; ++e) {
+            w[0][e] = w[1][e];
+            w[1][e] = w[2][e];
+            w[2][e] = sphi[(i + e % 3 - 1) + GE * ((j + e / 3 - 1) + GE * (k + 1))];
+          }
+          const R pc = w[1][4];
+          R out = kObstacle<R>();
+          if (!kSolid || !is_obstacle(pc)) {
             R acc = R(0.0);
 #pragma unroll
-            for (int pp = -1; pp <= 1; ++pp)
+            for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
-              for (int r = -1; r <= 1; ++r) {
-                const int ax = (a == 0) ? 1 : r, ay = (a == 0) ? r : (a == 1) ? 1 : pp,
-                          az = (a == 2) ? 1 : pp;
-                const int bx = (a == 0) ? -1 : ax, by = (a == 1) ? -1 : ay, bz = (a == 2) ? -1 : az;
-                const R rp = at(ax, ay, az), rm = at(bx, by, bz);
-                const R vp = is_obstacle(rp) ? pc : rp;
-                const R vm = is_obstacle(rm) ? pc : rm;
-                const R wt = (pp == 0 && r == 0) ? R(4.0) : (pp == 0 || r == 0) ? R(2.0) : R(1.0);
-                acc = acc + wt * (vp - vm);
-              }
-            nn[a] = acc;
+              for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                  const R raw = w[dz + 1][(dy + 1) * 3 + dx + 1];
+                  const R v = (kSolid && is_obstacle(raw)) ? pc : raw;
+                  acc = acc + k8w<R>(dx * dx + dy * dy + dz * dz) * v;
+                }
+            out = acc / wsum;
           }
-          const R len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) out[a] = (len > R(0.0)) ? nn[a] / len : R(0.0);
+          sps[(i - 1) + GS * ((j - 1) + GS * (k - 1))] = out;
         }
-        const int s3 = (i - 2) + GN * ((j - 2) + GN * (k - 2));
-        snh[s3] = out[0];
-        snh[GN * GN * GN + s3] = out[1];
-        snh[2 * GN * GN * GN + s3] = out[2];
       }
+      __syncthreads();
+      // Parker-Youngs normal on the 10^3 sub-box, z-columns as above
+      if (threadIdx.x < GN * GN) {
+        const int i = threadIdx.x % GN + 2, j = threadIdx.x / GN + 2;
+        auto psi = [&](int ii, int jj, int kk) { return sps[(ii - 1) + GS * ((jj - 1) + GS * (kk - 1))]; };
+        R w[3][9];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int e = 0; e < 9; ++e) w[q + 1][e] = psi(i + e % 3 - 1, j + e / 3 - 1, 1 + q);
+#pragma unroll
+        for (int k = 2; k < 2 + GN; ++k) {
+#pragma unroll
+          for (int e = 0; e < 9; ++e) {
+            w[0][e] = w[1][e];
+            w[1][e] = w[2][e];
+            w[2][e] = psi(i + e % 3 - 1, j + e / 3 - 1, k + 1);
+          }
+          auto at = [&](int dx, int dy, int dz) { return w[dz + 1][(dy + 1) * 3 + dx + 1]; };
+          const R pc = at(0, 0, 0);
+          R out[3] = {R(0.0), R(0.0), R(0.0)};
+          if (!kSolid || !is_obstacle(pc)) {
+            R nn[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              R acc = R(0.0);
+#pragma unroll
+              for (int pp = -1; pp <= 1; ++pp)
+#pragma unroll
+                for (int r = -1; r <= 1; ++r) {
+                  const int ax = (a == 0) ? 1 : r, ay = (a == 0) ? r : (a == 1) ? 1 : pp,
+                            az = (a == 2) ? 1 : pp;
+                  const int bx = (a == 0) ? -1 : ax, by = (a == 1) ? -1 : ay, bz = (a == 2) ? -1 : az;
+                  const R rp = at(ax, ay, az), rm = at(bx, by, bz);
+                  const R vp = (kSolid && is_obstacle(rp)) ? pc : rp;
+                  const R vm = (kSolid && is_obstacle(rm)) ? pc : rm;
+                  const R wt = (pp == 0 && r == 0) ? R(4.0) : (pp == 0 || r == 0) ? R(2.0) : R(1.0);
+                  acc = acc + wt * (vp - vm);
+                }
+              nn[a] = acc;
+            }
+            const R len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out[a] = (len > R(0.0)) ? nn[a] / len : R(0.0);
+          }
+          const int s3 = (i - 2) + GN * ((j - 2) + GN * (k - 2));
+          snh[s3] = out[0];
+          snh[GN * GN * GN + s3] = out[1];
+          snh[2 * GN * GN * GN + s3] = out[2];
+        }
+      }
+    };
+    if constexpr (sizeof(R) == 4) {
+      if (solid) planes32(std::true_type{});
+      else planes32(std::false_type{});
+    } else {
+      if (solid) stencils(std::true_type{});
+      else stencils(std::false_type{});
     }
     __syncthreads();
     // curvature, gas density and Thuerey class of the tile's interface cells
@@ -554,6 +696,42 @@ __global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) k_geometry(DPtrs d, 
     geometry_tile<Q, S>(d, p, d.tiles[parity][tt], g_smem);
 }
 
+// The bulk sweep with the geometry pass folded in (FP32 and 16-bit
+// engines).  Every kGeoFuseEvery-th block of the persistent grid first
+// takes geometry tiles, one at a time from a per-step counter (counts[7]:
+// zero at init, cleared again by the finalize kernel of every step), until
+// none is left, and then joins the other blocks on the bulk units.  The
+// tiles so run at the sweep's occupancy (four blocks of 256 threads per SM
+// instead of three of 192) with no launch boundary before the sweep.  On the
+// 160x160x1024 Taylor bubble: separate kernels 77.5 + 295 us, every block
+// first on tiles (1) 345 us, every second block (2) 364 us, every fourth
+// 361 us: the sweep needs all its blocks to keep HBM busy, so blocks held
+// by tiles slow it by about what running the tiles beside it saves.
+#ifndef FSLBM_GEO_FUSE_EVERY
+#define FSLBM_GEO_FUSE_EVERY 1
+#endif
+constexpr int kGeoFuseEvery = FSLBM_GEO_FUSE_EVERY;
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
+    k_bulk_geo(DPtrs d, KParams p, int parity) {
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  __shared__ int s_tile;
+  if (blockIdx.x == 0 && threadIdx.x == 0) reset_step_counts(d, parity);
+  if (blockIdx.x % kGeoFuseEvery == 0) {
+    const int ntiles = d.counts[3 + parity];
+    for (;;) {
+      __syncthreads();  // every thread has read the previous s_tile
+      if (threadIdx.x == 0) s_tile = atomicAdd(&d.counts[7], 1);
+      __syncthreads();
+      const int tt = s_tile;
+      if (tt >= ntiles) break;
+      geometry_tile<Q, S, kBulkBlock>(d, p, d.tiles[parity][tt], g_smem);
+    }
+  }
+  bulk_sweep<Q, S, COLL>(d, p, parity);
+}
+
 // ------------------------------------------------------- interface update
 // Directions whose neighbour data the mass exchange reads ahead at once, and
 // resident blocks of 128 threads per SM the FP32/FP16 interface kernels are
@@ -563,7 +741,7 @@ __global__ void __launch_bounds__(kGeoBlock, kGeoMinBlocks) k_geometry(DPtrs d, 
 // 107 us); the FP64 engine keeps two).  FSLBM_IFACE_MINB, when defined,
 // sets the bound for the FP32 and 16-bit engines.
 #ifndef FSLBM_IFACE_CHUNK
-#define FSLBM_IFACE_CHUNK 1
+#define FSLBM_IFACE_CHUNK 6
 #endif
 
 constexpr int kIfaceChunk = FSLBM_IFACE_CHUNK;
@@ -643,12 +821,16 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       if (st == T_GAS) f[i] = R(0.0);
     }
     // mass exchange with the streamed (not yet reconstructed) PDFs:
-    // a = f*_ibar(x + c_i) equals the pulled f_ibar(x).  With deviations the
-    // differences are taken in FP64 on the stored values (w_i = w_ibar
-    // cancels), so a liquid neighbour's PDF sum changes by exactly -dm_i.
+    // a = f*_ibar(x + c_i) equals the pulled f_ibar(x).  With deviations
+    // (w_i = w_ibar cancels) a liquid link's difference enters exactly, as a
+    // float pair, so a liquid neighbour's PDF sum changes by exactly -dm_i;
+    // an interface link's term is the float product of the same operands
+    // that the neighbour negates, so the two terms cancel exactly.
     const double phic = d.phi[c];
     const int clc = d.cls[c];
     double dm = 0.0;
+    FAcc acc;
+    const float phicf = d2f(phic);
     // class and fill level of the interface neighbours, read a chunk of
     // directions at a time ahead of the (ordered) accumulation
     constexpr int kChunk = kIfaceChunk;
@@ -673,17 +855,17 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
         const R fa = f[OPP(i)];
         const R fb = fx[i];
         if constexpr (S::kDev) {
-          const double ad = (double)fa, bd = (double)fb, w = W<Q, double>(i);
+          const float w = W<Q, float>(i);
           if (ntp == T_LIQ) {
-            dm = dm + (ad - bd);
+            acc.add_diff(fa, fb);
           } else {
             const int cln = cl9[a];
-            double v;
-            if (clc == cln) v = ad - bd;
-            else if (clc == CL_STD) v = (cln == CL_NF) ? ad + w : -(bd + w);
-            else if (clc == CL_NF) v = -(bd + w);
-            else v = ad + w;
-            dm = dm + 0.5 * (phic + ph9[a]) * v;
+            float v;
+            if (clc == cln) v = __fsub_rn(fa, fb);
+            else if (clc == CL_STD) v = (cln == CL_NF) ? __fadd_rn(fa, w) : -__fadd_rn(fb, w);
+            else if (clc == CL_NF) v = -__fadd_rn(fb, w);
+            else v = __fadd_rn(fa, w);
+            acc.add(__fmul_rn(__fmul_rn(0.5f, __fadd_rn(phicf, d2f(ph9[a]))), v));
           }
         } else {
           if (ntp == T_LIQ) {
@@ -700,6 +882,7 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
         }
       }
     }
+    if constexpr (S::kDev) dm = acc.value();
     const double mn = d.mass[c] + dm;
     // BC velocity from the cell's own post-collision PDFs
     R rc, jx, jy, jz;
@@ -758,13 +941,15 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
         }
         sd = (double)n * (1.0 / (double)(1LL << S::kShift));
       } else {
+        FAcc sa;  // the float sum carried as a pair: FP64 accuracy, FP32 operations
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           const T v = S::stored(f[i]);
           B[(long long)i * Np + c] = v;
           fs[i] = S::loadd(v);
-          sd += (double)fs[i];
+          sa.add(fs[i]);
         }
+        sd = sa.value();
       }
       rho = 1.0 + sd;
       R r0, jx0, jy0, jz0;
@@ -794,7 +979,17 @@ __device__ __forceinline__ void interface_cell(const DPtrs& d, const KParams& p,
       const uint8_t fl = flags[c];
       if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], (fl & F_WRAP) != 0, f);
     }
-    const double phin = mn / rho;
+    double phin;
+    if constexpr (S::kDev) {
+      // mn / rho from the float reciprocal and one Newton step in FP64
+      // (relative error about 2^-46; an FP64 division takes tens of FP64
+      // operations)
+      const double r0 = (double)__frcp_rn(d2f(rho));
+      const double q0 = mn * r0;
+      phin = fma(fma(-q0, rho, mn), r0, q0);
+    } else {
+      phin = mn / rho;
+    }
     d.m_next[k] = mn;
     d.phi_next[k] = phin;
     d.rho_band[k] = rho;
@@ -1290,7 +1485,10 @@ __device__ __forceinline__ void finalize_warp(const DPtrs& d, const KParams& p, 
 
 static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, int parity) {
   const int total = d.counts[parity] + d.counts[2];
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.counts[6] = 0;  // the next step's bulk hand-out
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.counts[6] = 0;  // the next step's bulk hand-out
+    d.counts[7] = 0;  // and geometry-tile hand-out
+  }
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int base = wid * 32; base < total; base += warps * 32) finalize_warp(d, p, parity, base);
@@ -1462,7 +1660,10 @@ __device__ __forceinline__ int round32(int v) { return (v + 31) & ~31; }
 // fills and lays out tiles, bulk warp units and band cells.
 static __global__ void kb_plan_front(DomRec* recs, BatchPlan pl) {
   constexpr int kGroups = 32 / kSegCells;
-  if (threadIdx.x == 0) *(pl.all + pl.n + 1) = 0;  // kb_bulk's hand-out counter
+  if (threadIdx.x == 0) {
+    *(pl.all + pl.n + 1) = 0;  // the bulk sweep's hand-out counter
+    *(pl.all + pl.n + 2) = 0;  // and the fused sweep's tile counter
+  }
   for (int k = threadIdx.x; k < pl.n; k += blockDim.x) reset_step_counts(recs[k].d, recs[k].parity);
   __syncthreads();
   block_prefix(pl.n, pl.tiles, [&](int k) { return recs[k].d.counts[3 + recs[k].parity]; });
@@ -1494,8 +1695,7 @@ __device__ __forceinline__ int* batch_bulk_ctr(const BatchPlan& pl) { return pl.
 
 // Units of all domains handed out as in k_bulk, kBulkChunk at a time.
 template <int Q, class S, int COLL>
-__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
-    kb_bulk(const DomRec* __restrict__ recs, BatchPlan pl) {
+__device__ __forceinline__ void batch_bulk_sweep(const DomRec* __restrict__ recs, const BatchPlan& pl) {
   const int total = pl.bulk[pl.n];
   auto unit = [&](int w) {
     const int k = find_domain(pl.bulk, pl.n, w);
@@ -1515,6 +1715,36 @@ __global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
     const int warps = (gridDim.x * kBulkBlock) >> 5;
     for (int w = (blockIdx.x * kBulkBlock + threadIdx.x) >> 5; w < total; w += warps) unit(w);
   }
+}
+
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
+    kb_bulk(const DomRec* __restrict__ recs, BatchPlan pl) {
+  batch_bulk_sweep<Q, S, COLL>(recs, pl);
+}
+
+// The batch's bulk sweep with the geometry tiles of all domains folded in,
+// as k_bulk_geo: the blocks first take tiles from the plan's tile counter
+// (the int after the bulk hand-out counter), then bulk units.
+template <int Q, class S, int COLL>
+__global__ void __launch_bounds__(kBulkBlock, (bulk_min_blocks<S, COLL>()))
+    kb_bulk_geo(const DomRec* __restrict__ recs, BatchPlan pl) {
+  extern __shared__ __align__(16) unsigned char g_smem[];
+  __shared__ int s_tile;
+  if (blockIdx.x % kGeoFuseEvery == 0) {
+    const int total = pl.tiles[pl.n];
+    for (;;) {
+      __syncthreads();  // every thread has read the previous s_tile
+      if (threadIdx.x == 0) s_tile = atomicAdd(batch_bulk_ctr(pl) + 1, 1);
+      __syncthreads();
+      const int t = s_tile;
+      if (t >= total) break;
+      const int k = find_domain(pl.tiles, pl.n, t);
+      const DomRec& r = recs[k];
+      geometry_tile<Q, S, kBulkBlock>(r.d, r.p, r.d.tiles[r.parity][t - pl.tiles[k]], g_smem);
+    }
+  }
+  batch_bulk_sweep<Q, S, COLL>(recs, pl);
 }
 
 template <int Q, class S, int COLL>

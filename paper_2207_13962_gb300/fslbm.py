@@ -42,6 +42,10 @@ class fslbm_tuning(C.Structure):
                 ("ms_per_step", C.c_double)]
 
 
+class fslbm_front_stats(C.Structure):
+    _fields_ = [("count", C.c_int64), ("r_min", C.c_double), ("r_max", C.c_double), ("r_mean", C.c_double)]
+
+
 class fslbm_obs(C.Structure):
     _fields_ = [("step", C.c_int64), ("total_mass", C.c_double), ("n_liquid", C.c_int64),
                 ("n_interface", C.c_int64), ("n_gas", C.c_int64), ("n_obstacle", C.c_int64),
@@ -78,7 +82,7 @@ _lock = threading.Lock()
 
 # Exported symbols (kept in sync with include/fslbm.h by a CPU test).
 SYMBOLS = ["fslbm_params_default", "fslbm_create", "fslbm_init", "fslbm_step", "fslbm_sync",
-           "fslbm_observables", "fslbm_read_fields", "fslbm_bubbles", "fslbm_set_timing",
+           "fslbm_observables", "fslbm_front", "fslbm_read_fields", "fslbm_bubbles", "fslbm_set_timing",
            "fslbm_stage_times", "fslbm_save", "fslbm_load", "fslbm_interface_count", "fslbm_work_counts",
            "fslbm_observables_noalloc", "fslbm_set_axis_order", "fslbm_get_axis_order", "fslbm_destroy", "fslbm_last_error", "fslbm_version",
            "fslbm_batch_create", "fslbm_batch_step", "fslbm_batch_sync", "fslbm_batch_autotune",
@@ -114,6 +118,8 @@ def load(build_if_missing: bool = True):
         lib.fslbm_sync.restype = i
         lib.fslbm_observables.argtypes = [p, C.POINTER(fslbm_obs)]
         lib.fslbm_observables.restype = i
+        lib.fslbm_front.argtypes = [p, i, d, d, C.POINTER(fslbm_front_stats), p]
+        lib.fslbm_front.restype = i
         lib.fslbm_read_fields.argtypes = [p, p, p, p, p]
         lib.fslbm_read_fields.restype = i
         lib.fslbm_bubbles.argtypes = [p, p, p, i, C.POINTER(i)]
@@ -287,6 +293,20 @@ class Context:
         if check and st not in (OK, EUNSTABLE):
             self._check(st)
         return {k: getattr(o, k) for k, _ in fslbm_obs._fields_} | {"status": st}
+
+    def front(self, layer, center, mask=False):
+        """Seed-fill front of the z-layer ``layer`` (fslbm_front): a dict with
+        count, r_min, r_max, r_mean about ``center`` = (xc, yc), plus the front
+        mask [ny, nx] of bools when ``mask``."""
+        st = fslbm_front_stats()
+        nx, ny = self.shape[0], self.shape[1]
+        m = np.zeros(nx * ny, np.uint8) if mask else None
+        self._check(self.lib.fslbm_front(self.h, int(layer), float(center[0]), float(center[1]), C.byref(st),
+                                         _ptr(m)))
+        out = {k: getattr(st, k) for k, _ in fslbm_front_stats._fields_}
+        if mask:
+            out["mask"] = m.reshape(ny, nx).astype(bool)
+        return out
 
     def read(self, pdf=True):
         out = {"fill": np.zeros(self.N, np.float64), "flags": np.zeros(self.N, np.uint8),

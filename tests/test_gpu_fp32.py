@@ -89,3 +89,20 @@ def test_fp32_error_is_not_zero(gpu_lib):
     sc = S.random_interface(shape=(24, 18, 9), seed=3, g=1e-3)
     dp, _, _ = _run(sc, 1)
     assert dp > 1e-9
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_fp32_obstacle_free_tiles(q, gpu_lib):
+    """Surface tension dominates the gas density (sigma = 2e-2) on a surface
+    whose geometry tiles hold no obstacle and no position outside the
+    domain (periodic x and z, the surface far from the y walls): the FP32
+    engine evaluates the K8 smoothing and the Parker-Youngs normal there in
+    their plane-by-plane form.  A wrong weight or sign in either changes
+    kappa by O(0.1), rho^G = 3 (p^V + sigma kappa) by O(1e-3) and the
+    reconstructed PDFs by far more than the FP32 bound."""
+    sc = S.random_interface(shape=(40, 48, 24), seed=11, q=q, variant="OM", g=1e-4, sigma=2e-2,
+                            periodic=(True, False, True), obstacles=False, amp=4.0)
+    dp, dfill, dm = _run(sc, 2)
+    print(f"FP32 vs FP64 oracle, obstacle-free tiles, D3Q{q}: pdf {dp:.2e} fill {dfill:.2e} mass {dm:.2e}")
+    assert dp <= 2 * PDF_TOL_STEP, dp
+    assert dfill <= 2 * MASS_TOL_STEP and dm <= 2 * MASS_TOL_STEP, (dfill, dm)

@@ -200,6 +200,17 @@ def test_timing_mode_matches_graph_mode(gpu_lib):
     np.testing.assert_array_equal(ra["pdf"], rb["pdf"])
     times, launches = b.stage_times()
     assert launches == 20 * 7 and times["bulk"] > 0
+    # the FP32 engine folds the geometry pass into the bulk sweep: one launch
+    # less a step, the same results in both modes
+    a = fslbm.context_for(sc, precision="FP32")
+    b = fslbm.context_for(sc, precision="FP32")
+    b.set_timing(True)
+    a.step(20)
+    b.step(20)
+    ra, rb = a.read(), b.read()
+    np.testing.assert_array_equal(ra["pdf"], rb["pdf"])
+    times, launches = b.stage_times()
+    assert launches == 20 * 6 and times["bulk"] > 0
 
 
 def test_reinit_matches_fresh_context(gpu_lib):
