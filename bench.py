@@ -675,48 +675,79 @@ def bench_serve(args, emit=True):
 
 # ------------------------------------------- observables of reduced precision
 
+def _perturbed(sc, seed=1, size=1e-7):
+    """The scenario with its interface cells' fill levels moved by a seeded
+    uniform +-size (the conditioning floor: how far an observable moves
+    under a perturbation of FP32-rounding size)."""
+    import dataclasses
+    from paper_2207_13962_gb300 import scenarios as S
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fill = sc.fill.copy()
+    m = sc.flags == S.IFACE
+    fill[m] = np.clip(fill[m] + rng.uniform(-size, size, int(m.sum())), 0.0, 1.0)
+    return dataclasses.replace(sc, fill=fill)
+
+
 def dam_break_observables(args):
-    """The rectangular dam break 256x128x64 (D3Q19 TRT, nu = 1e-3, no-slip
-    box, liquid column x < 64, y < 64 over the full depth, g = 1e-5): for each
-    BC variant, the FP64 run (the parity mode) against FP32 and the
-    mass-conserving formats.  Observables every 100 steps on the mid-depth
-    plane z = 32: front w(t) = sum_i phi(i, 0, 32) and column height
-    h(t) = sum_j phi(0, j, 32); errors max_t |x(t) - x_64(t)| / x_64(t)."""
+    """The rectangular dam break 256x128x64 (D3Q19, liquid column x < 64,
+    y < 64 over the full depth, g = 1e-5): for each BC variant, the FP64 run
+    (the parity mode) against FP32 and the mass-conserving formats, and
+    against the FP64 run from fill levels perturbed by 1e-7 (the observable's
+    conditioning floor).  Observables every 100 steps on the mid-depth plane
+    z = 32: front w(t) = sum_i phi(i, 0, 32) and column height
+    h(t) = sum_j phi(0, j, 32); errors max_t |x(t) - x_64(t)| / x_64(t).
+    The configs' setup: TRT, nu = 1e-3, no-slip box.  With --paper-walls,
+    the paper's (Sec. 4.2): free-slip walls at all borders, SRT with
+    omega = 1.9995 and the Smagorinsky model with C_S = 0.1."""
     import torch
     from paper_2207_13962_gb300 import fslbm
     from paper_2207_13962_gb300 import scenarios as S
     torch.cuda.set_device(0)
     steps, every = args.obs_steps, 100
+    over = {}
+    if args.paper_walls:
+        over = dict(periodic=(2, 2, 2), collision="SRT", omega=1.9995, smagorinsky_cs=0.1)
     out = {}
     for variant in ("NBRC", "NBKC", "OM", "OM3"):
         sc = S.dam_break(variant=variant)
         nx, ny, nz = sc.shape
         series = {}
-        for prec in ("FP64", "FP32", "FP32MC", "FP16SMC"):
-            c = fslbm.context_for(sc, precision=prec)
+        for prec, scn in (("FP64", sc), ("FP64_perturbed", _perturbed(sc)), ("FP32", sc), ("FP32MC", sc),
+                          ("FP16SMC", sc)):
+            c = fslbm.context_for(scn, precision=prec.split("_")[0], **over)
             M0 = c.observables()["total_mass"]
             w, h, status, t0 = [], [], 0, time.perf_counter()
             for _ in range(steps // every):
                 c.step(every)
+                if c.sync() != 0:  # unstable (EUNSTABLE): the series stops here
+                    break
                 f = c.read(pdf=False)["fill"].reshape(nz, ny, nx)[nz // 2]
                 w.append(float(f[0].sum()))
                 h.append(float(f[:, 0].sum()))
-            obs = c.observables()
+            obs = c.observables(check=False)
             status = obs["status"]
             c.close()
             series[prec] = (np.array(w), np.array(h), status, abs(obs["total_mass"] - M0) / M0,
                             time.perf_counter() - t0)
         ref = series["FP64"]
-        res = {"FP64": {"status": ref[2], "front_final": ref[0][-1], "height_final": ref[1][-1],
+        res = {"FP64": {"status": ref[2], "steps_stable": every * len(ref[0]),
+                        "front_final": ref[0][-1] if len(ref[0]) else None,
+                        "height_final": ref[1][-1] if len(ref[1]) else None,
                         "mass_drift_rel": ref[3], "seconds": round(ref[4], 2)}}
-        for prec in ("FP32", "FP32MC", "FP16SMC"):
+        for prec in ("FP64_perturbed", "FP32", "FP32MC", "FP16SMC"):
             w, h, st, drift, sec = series[prec]
-            res[prec] = {"status": st, "front_rel_err": float(np.max(np.abs(w - ref[0]) / ref[0])),
-                         "height_rel_err": float(np.max(np.abs(h - ref[1]) / ref[1])),
-                         "mass_drift_rel": drift, "seconds": round(sec, 2)}
+            n = min(len(w), len(ref[0]))  # compare where both are stable
+            res[prec] = {"status": st, "steps_stable": every * len(w),
+                         "front_rel_err": float(np.max(np.abs(w[:n] - ref[0][:n]) / ref[0][:n])) if n else None,
+                         "height_rel_err": float(np.max(np.abs(h[:n] - ref[1][:n]) / ref[1][:n])) if n else None,
+                         "compared_steps": every * n, "mass_drift_rel": drift, "seconds": round(sec, 2)}
         out[variant] = res
-    line = {"metric": METRIC, "workload": f"dam break 256x128x64 observables, {steps} steps",
-            "results": out, "data": "synthetic (seeded generator, no dataset)"}
+    setup = ("free-slip walls, SRT omega 1.9995, Smagorinsky C_S 0.1 (the paper's Sec. 4.2)" if args.paper_walls
+             else "no-slip box, TRT nu 1e-3 (the configs')")
+    line = {"metric": METRIC, "workload": f"dam break 256x128x64 observables, {steps} steps, {setup}",
+            "results": out, "floor": "FP64_perturbed: the FP64 run from interface fill levels moved by a seeded "
+                                     "+-1e-7",
+            "data": "synthetic (seeded generator, no dataset)"}
     print(json.dumps(line), flush=True)
     return line
 
@@ -725,7 +756,9 @@ def taylor_rise(args):
     """Rise velocity of the Taylor bubble 160x160x1024 (D3Q19 TRT OM, bubble
     model): the bubble centroid z_c = sum (1 - phi) z / sum (1 - phi) over gas
     and interface cells, every 1000 steps, and the rise velocity dz_c/dt over
-    the last quarter of the run; FP32 against the mass-conserving formats."""
+    the last quarter of the run; the FP64 run (the parity mode) against FP32
+    and the mass-conserving formats, and against the FP64 run from fill
+    levels perturbed by 1e-7 (the observable's conditioning floor)."""
     import torch
     from paper_2207_13962_gb300 import fslbm
     from paper_2207_13962_gb300 import scenarios as S
@@ -735,8 +768,9 @@ def taylor_rise(args):
     zc_of = np.arange(nz, dtype=np.float64)[:, None, None] + 0.5
     steps, every = args.rise_steps, 1000
     out = {}
-    for prec in ("FP32", "FP32MC", "FP16SMC"):
-        c = fslbm.context_for(sc, precision=prec)
+    for prec, scn in (("FP64", sc), ("FP64_perturbed", _perturbed(sc)), ("FP32", sc), ("FP32MC", sc),
+                      ("FP16SMC", sc)):
+        c = fslbm.context_for(scn, precision=prec.split("_")[0])
         M0 = c.observables()["total_mass"]
         t, z, t0 = [], [], time.perf_counter()
         for k in range(steps // every):
@@ -753,10 +787,11 @@ def taylor_rise(args):
         vel = float(np.polyfit(t[-q:], z[-q:], 1)[0])
         out[prec] = {"rise_velocity": vel, "centroid_final": z[-1], "status": obs["status"],
                      "mass_drift_rel": abs(obs["total_mass"] - M0) / M0, "seconds": round(time.perf_counter() - t0, 1)}
-    for prec in ("FP32MC", "FP16SMC"):
-        out[prec]["rise_velocity_rel_err_vs_fp32"] = abs(out[prec]["rise_velocity"] - out["FP32"]["rise_velocity"]) / \
-            abs(out["FP32"]["rise_velocity"])
+    for prec in ("FP64_perturbed", "FP32", "FP32MC", "FP16SMC"):
+        out[prec]["rise_velocity_rel_err_vs_fp64"] = abs(out[prec]["rise_velocity"] - out["FP64"]["rise_velocity"]) / \
+            abs(out["FP64"]["rise_velocity"])
     line = {"metric": METRIC, "workload": f"Taylor bubble rise velocity, {steps} steps", "results": out,
+            "floor": "FP64_perturbed: the FP64 run from interface fill levels moved by a seeded +-1e-7",
             "data": "synthetic (seeded generator, no dataset)"}
     print(json.dumps(line), flush=True)
     return line
@@ -849,6 +884,8 @@ def main(argv=None):
                                                        "taylor_rise"])
     ap.add_argument("--obs-steps", type=int, default=20000, help="dam_break_observables: steps")
     ap.add_argument("--rise-steps", type=int, default=100000, help="taylor_rise: steps")
+    ap.add_argument("--paper-walls", action="store_true",
+                    help="dam_break_observables: free-slip walls, SRT omega 1.9995, Smagorinsky C_S 0.1")
     ap.add_argument("--precision", default="FP32", choices=list(S_BYTES))
     ap.add_argument("--variant", default="OM", choices=["NBRC", "NBKC", "OM", "OM3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -127,6 +127,21 @@ typedef struct {
                          tau = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C_S^2 Qbar / rho)) / 2
                          from the non-equilibrium momentum flux Qbar of the
                          PDFs entering the collision; TRT keeps trt_magic  */
+  int bubble_relabel_every; /* bubble coalescence and segmentation (the bubble
+                         model Sec. 2.2 cites follows them), every K steps
+                         after init; 0 (default): the bubbles stay those of
+                         the initial state.  With the bubble model on, the
+                         bubbles become the connected gas regions of the
+                         current flags (as at init), and each old bubble's
+                         gas, whose amount is p^V V = p^V(0) V(0), goes to
+                         the new bubbles in proportion to the volume of its
+                         cells that each holds (fixed point, exact sums; a
+                         bubble none of whose cells is in a new one has
+                         vanished with its gas):
+                         merging bubbles keep sum p^V V, the parts of a split
+                         bubble keep its pressure, and gas or interface cells
+                         outside every bubble bring their volume at p^V(0).
+                         Single-domain contexts only (batches reject it). */
 } fslbm_params;
 
 /* Whole-domain observables (FP64 reductions on the device). */

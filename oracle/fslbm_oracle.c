@@ -96,6 +96,18 @@
  *       interface cell of the layer with a reached gas cell among its
  *       in-plane face neighbours.  Its radius is the distance of its cell
  *       centre (x + 1/2, y + 1/2) to the given centre (xc, yc).
+ *   R24 bubble coalescence and segmentation (Sec. 2.2 cites a bubble model
+ *       that follows them, without the algorithm): every K steps (K = 0, the
+ *       default, keeps the labels of the initial state) the bubbles are
+ *       relabelled from the current flags as at init (R19), and each old
+ *       bubble's gas, whose amount is p^V V = p^V(0) V0, is divided over the
+ *       new bubbles in proportion to the fixed-point volume of its cells that
+ *       each holds (a bubble none of whose cells is in a new bubble has
+ *       vanished with its gas).  Merging bubbles so keep the sum of p^V V
+ *       (Boyle's law at equal temperature), and the parts of a split bubble
+ *       keep its pressure.  Cells without an old id (gas or interface cells
+ *       outside every bubble, which the step gives the pressure p^V(0)) bring
+ *       their volume at p^V(0), so a new gas region starts at p^V(0).
  *
  * R8 has one exception: a gas cell that becomes interface gets f^eq of the
  * mean density and velocity of its neighbours (R14), with no collision, so
@@ -411,6 +423,7 @@ struct orc {
   double* rho;               /* density of this step's collision (scratch) */
   int* bid;                  /* bubble id (gas/interface), -1 otherwise */
   int nb;                    /* number of bubbles */
+  int relabel_every;         /* steps between bubble relabellings (R24), 0: never */
   double *V0, *pV;           /* per bubble */
   long step;
   /* scratch */
@@ -596,6 +609,49 @@ static void bubble_volumes(const orc* o, double* V) {
   free(acc);
 }
 
+/* Bubble labels of the current flags (R19): the connected gas components
+ * (lattice neighbourhood, periodic wrap) numbered in the order of their
+ * lowest cell index; an interface cell takes the lowest id among its gas
+ * neighbours (-1 without one); every other cell -1.  Returns the count. */
+static int label_bubbles(orc* o) {
+  const lattice* L = &o->L;
+  const long N = o->N;
+  long c;
+  int i, x, y, z, nb = 0;
+  long* stack = (long*)malloc(sizeof(long) * (size_t)(N > 0 ? N : 1));
+  for (c = 0; c < N; ++c) o->bid[c] = -1;
+  for (c = 0; c < N; ++c) {
+    long sp = 0;
+    if (o->flag[c] != GAS || o->bid[c] >= 0) continue;
+    o->bid[c] = nb;
+    stack[sp++] = c;
+    while (sp > 0) {
+      long a = stack[--sp];
+      coords(o, a, &x, &y, &z);
+      for (i = 1; i < L->q; ++i) {
+        long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
+        if (n >= 0 && o->flag[n] == GAS && o->bid[n] < 0) {
+          o->bid[n] = nb;
+          stack[sp++] = n;
+        }
+      }
+    }
+    ++nb;
+  }
+  free(stack);
+  for (c = 0; c < N; ++c) {
+    int best = -1;
+    if (o->flag[c] != IFACE) continue;
+    coords(o, c, &x, &y, &z);
+    for (i = 1; i < L->q; ++i) {
+      long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
+      if (n >= 0 && o->flag[n] == GAS && (best < 0 || o->bid[n] < best)) best = o->bid[n];
+    }
+    o->bid[c] = best;
+  }
+  return nb;
+}
+
 int orc_init(orc* o, const double* fill, const unsigned char* flags,
              const double* velocity, const double* density) {
   const lattice* L = &o->L;
@@ -630,39 +686,7 @@ int orc_init(orc* o, const double* fill, const unsigned char* flags,
   }
   /* bubble labels: connected gas components in order of lowest index (R19) */
   {
-    long* stack = (long*)malloc(sizeof(long) * (size_t)N);
-    int nb = 0;
-    for (c = 0; c < N; ++c) o->bid[c] = -1;
-    for (c = 0; c < N; ++c) {
-      long sp = 0;
-      if (o->flag[c] != GAS || o->bid[c] >= 0) continue;
-      o->bid[c] = nb;
-      stack[sp++] = c;
-      while (sp > 0) {
-        long a = stack[--sp];
-        coords(o, a, &x, &y, &z);
-        for (i = 1; i < L->q; ++i) {
-          long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
-          if (n >= 0 && o->flag[n] == GAS && o->bid[n] < 0) {
-            o->bid[n] = nb;
-            stack[sp++] = n;
-          }
-        }
-      }
-      ++nb;
-    }
-    free(stack);
-    for (c = 0; c < N; ++c) {
-      int best = -1;
-      if (o->flag[c] != IFACE) continue;
-      coords(o, c, &x, &y, &z);
-      for (i = 1; i < L->q; ++i) {
-        long n = nbr(o, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
-        if (n >= 0 && o->flag[n] == GAS && (best < 0 || o->bid[n] < best))
-          best = o->bid[n];
-      }
-      o->bid[c] = best;
-    }
+    const int nb = label_bubbles(o);
     o->nb = nb;
     free(o->V0);
     free(o->pV);
@@ -1068,8 +1092,73 @@ static void bubble_pressure(orc* o) {
   free(V);
 }
 
+/* Bubble coalescence and segmentation (R24): the bubbles become the
+ * connected gas regions of the current flags (label_bubbles), and the gas
+ * of every old bubble A, whose amount is proportional to p^V_A V_A =
+ * p^V(0) V0_A, goes to the new bubbles in proportion to the volume of A's
+ * cells that each holds: V0_C = sum over A (ascending) of
+ * V0_A * (vol(A and C) / vol(A handed on)), plus vol(C's cells without an
+ * id), volumes in the fixed point of R19, vol(A handed on) over the cells
+ * of A that are in a new bubble.  Then p^V = p^V(0) V0 / V. */
+static void relabel_bubbles(orc* o) {
+  const long N = o->N;
+  const int nb_old = o->nb;
+  int* old = (int*)malloc(sizeof(int) * (size_t)(N > 0 ? N : 1));
+  int64_t *M, *row;
+  double *V0n, *pVn;
+  int nb_new, A, C, W;
+  long c;
+  memcpy(old, o->bid, sizeof(int) * (size_t)N);
+  nb_new = label_bubbles(o);
+  W = nb_new + 1; /* column 0: cells that end in no bubble */
+  M = (int64_t*)calloc((size_t)(nb_old > 0 ? nb_old : 1) * (size_t)W, sizeof(int64_t));
+  row = (int64_t*)calloc((size_t)(nb_old > 0 ? nb_old : 1), sizeof(int64_t));
+  /* free[C]: volume of the cells of new bubble C that carried no id */
+  int64_t* fr = (int64_t*)calloc((size_t)(nb_new > 0 ? nb_new : 1), sizeof(int64_t));
+  for (c = 0; c < N; ++c) {
+    int64_t v;
+    A = old[c];
+    if (o->flag[c] == GAS)
+      v = (int64_t)4294967296LL;
+    else if (o->flag[c] == IFACE)
+      v = vol_fix(1.0 - o->phi[c]);
+    else
+      continue;
+    if (A < 0) {
+      if (o->bid[c] >= 0) fr[o->bid[c]] += v;
+      continue;
+    }
+    M[(size_t)A * W + (size_t)(o->bid[c] + 1)] += v;
+    if (o->bid[c] >= 0) row[A] += v; /* the volume A hands on to new bubbles */
+  }
+  V0n = (double*)calloc((size_t)(nb_new > 0 ? nb_new : 1), sizeof(double));
+  pVn = (double*)calloc((size_t)(nb_new > 0 ? nb_new : 1), sizeof(double));
+  for (C = 0; C < nb_new; ++C) {
+    double s = 0.0;
+    for (A = 0; A < nb_old; ++A) {
+      const int64_t m = M[(size_t)A * W + (size_t)(C + 1)];
+      if (m == 0 || row[A] == 0) continue;
+      s = s + o->V0[A] * ((double)m / (double)row[A]);
+    }
+    /* cells without an id hold gas at p^V(0), like the gas cells outside
+       every bubble (their pressure is p^V(0) in the step) */
+    V0n[C] = s + (double)fr[C] / 4294967296.0;
+  }
+  free(fr);
+  free(o->V0);
+  free(o->pV);
+  o->V0 = V0n;
+  o->pV = pVn;
+  o->nb = nb_new;
+  free(M);
+  free(row);
+  free(old);
+  bubble_pressure(o);
+}
+
 /* One FSLBM time step: geometry -> stream/BC/mass/collide -> conversion and
- * excess mass -> bubble pressure. */
+ * excess mass -> bubble pressure (and, every relabel_every steps, bubble
+ * coalescence and segmentation). */
 static void one_step(orc* o) {
   double* t;
   geometry(o);
@@ -1081,6 +1170,13 @@ static void one_step(orc* o) {
   o->fn = t;
   bubble_pressure(o);
   o->step += 1;
+  if (o->bubble_model && o->relabel_every > 0 && o->step % o->relabel_every == 0) relabel_bubbles(o);
+}
+
+void orc_set_bubble_relabel(orc* o, int every) { o->relabel_every = every > 0 ? every : 0; }
+
+void orc_relabel_bubbles(orc* o) {
+  if (o->bubble_model) relabel_bubbles(o);
 }
 
 void orc_step(orc* o, int n) {

@@ -40,6 +40,11 @@ void orc_destroy(orc* o);
 int orc_init(orc* o, const double* fill, const unsigned char* flags,
              const double* velocity, const double* density);
 void orc_step(orc* o, int n);
+/* Bubble coalescence and segmentation (reading R24) every `every` steps
+ * after init (0, the default: the labels of the initial state stay). */
+void orc_set_bubble_relabel(orc* o, int every);
+/* The same relabelling once, now (bubble model only). */
+void orc_relabel_bubbles(orc* o);
 long orc_steps_done(const orc* o);
 
 /* Any pointer may be NULL.  pdf[q*N] direction-major post-collision PDFs. */

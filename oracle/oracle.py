@@ -83,6 +83,10 @@ def _load(openmp: bool = False):
         lib.orc_seed_fill_front.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, p, C.c_int,
                                             C.c_double, C.c_double, p, p]
         lib.orc_seed_fill_front.restype = C.c_int
+        lib.orc_set_bubble_relabel.argtypes = [p, C.c_int]
+        lib.orc_set_bubble_relabel.restype = None
+        lib.orc_relabel_bubbles.argtypes = [p]
+        lib.orc_relabel_bubbles.restype = None
         if openmp:
             _lib_omp = lib
         else:
@@ -188,15 +192,16 @@ class Oracle:
     boundary of each axis (``periodic``: 0 / False no-slip walls, 1 / True
     periodic, 2 free-slip walls), q (19/27), collision ('SRT'/'TRT'), variant
     ('NBRC'/'NBKC'/'OM'/'OM3'), OM3 fallback, bubble model, omega, TRT magic
-    parameter, gravity g[3], surface tension sigma, eps_phi, p_v0.
-    ``openmp`` runs the stream-collide cell loop on all host threads (the
+    parameter, gravity g[3], surface tension sigma, eps_phi, p_v0, the
+    Smagorinsky constant and the steps between bubble relabellings (reading
+    R24; 0 keeps the initial labels).  ``openmp`` runs the stream-collide cell loop on all host threads (the
     OpenMP build of the same source; same results).
     """
 
     def __init__(self, nx, ny, nz, periodic=(False, False, False), q=19, collision="TRT",
                  variant="OM", om3_fallback="NBKC", bubble_model=False, omega=1.0,
                  trt_magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), sigma=0.0, eps_phi=1e-2,
-                 p_v0=1.0 / 3.0, smagorinsky_cs=0.0, openmp=False):
+                 p_v0=1.0 / 3.0, smagorinsky_cs=0.0, bubble_relabel_every=0, openmp=False):
         self._lib = _load(openmp)
         self.shape = (int(nx), int(ny), int(nz))
         self.N = int(nx) * int(ny) * int(nz)
@@ -212,6 +217,11 @@ class Oracle:
         if not h:
             raise ValueError("oracle: invalid parameters")
         self._h = h
+        self._lib.orc_set_bubble_relabel(h, int(bubble_relabel_every))
+
+    def relabel_bubbles(self):
+        """Bubble coalescence and segmentation now (reading R24)."""
+        self._lib.orc_relabel_bubbles(self._h)
 
     def __del__(self):
         h = getattr(self, "_h", None)

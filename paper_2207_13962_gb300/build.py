@@ -62,8 +62,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    # host code without floating-point contraction too: the bubble relabelling
+    # divides the gas on the host in the oracle's order of operations, and an
+    # Arm host compiler would otherwise fuse its multiply-adds
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                     "-I", os.path.join(os.path.dirname(HERE), "include")]
+                     "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(os.path.dirname(HERE), "include")]
     if extra_flags:
         common += list(extra_flags)
 

@@ -161,6 +161,7 @@ fslbm_status fslbm_create(const fslbm_domain* domain, fslbm_lattice lattice,
   for (int a = 0; a < 3; ++a)
     if (!valid_enum(domain->periodic[a], FSLBM_NO_SLIP, FSLBM_FREE_SLIP)) return FSLBM_EINVAL;
   if (!(params->smagorinsky_cs >= 0.0)) return FSLBM_EINVAL;
+  if (params->bubble_relabel_every < 0) return FSLBM_EINVAL;
   if (!valid_enum(params->precision, 0, 5)) return FSLBM_EINVAL;
   if (params->om3_fallback != FSLBM_NBRC && params->om3_fallback != FSLBM_NBKC) return FSLBM_EINVAL;
   if (!(params->omega > 0.0 && params->omega < 2.0)) return FSLBM_EINVAL;
@@ -520,6 +521,7 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   }
   d.nb = nb;
   const size_t nbb = (size_t)(nb > 0 ? nb : 1);
+  c->nb_cap = (int)nbb;
   if (e == cudaSuccess) e = dalloc(c, &d.V0, nbb * sizeof(double));
   if (e == cudaSuccess) e = dalloc(c, &d.pV, nbb * sizeof(double));
   if (e == cudaSuccess) e = dalloc(c, &d.gas_cnt, nbb * sizeof(long long));
@@ -576,6 +578,133 @@ fslbm_status fslbm_init(fslbm_ctx* c, const double* fill, const uint8_t* flags,
   return FSLBM_OK;
 }
 
+// Bubble coalescence and segmentation between steps (fslbm_params::
+// bubble_relabel_every): the bubbles are labelled again from the current
+// flags with the kernels of init; the overlap of old and new bubbles (in
+// 2^-32 fixed point, exact integer sums) comes to the host, which divides
+// each old bubble's gas reference V0 over the new ones in proportion to the
+// volume of its cells that each holds (in the oracle's order of operations:
+// ascending old id), adds the volume of cells that carried no id (gas at
+// p^V(0)), and uploads the new V0; the new bubbles' volumes and pressures
+// follow.  The step's scratch lists serve as work space (free between
+// steps).  The graphs are captured again when the bubble count changes.
+namespace {
+fslbm_status relabel_bubbles(fslbm_ctx* c) {
+  DPtrs& d = c->d;
+  const KParams& k = c->kp;
+  cudaStream_t st = c->stream;
+  const int N = k.N;
+  const int gcells = (N + kBlock - 1) / kBlock;
+  const int nchunks = (N + kCcChunk - 1) / kCcChunk;
+  int* lab = d.band[c->parity ^ 1];
+  int* root_id = d.newlist;
+  int* old_bid = (int*)d.m_next;
+  uint8_t* raw = (uint8_t*)d.phi_next;
+  const int nb_old = d.nb;
+  int *cnt = nullptr, *off = nullptr;
+  cudaError_t e = cudaMemcpyAsync(old_bid, d.bid, (size_t)N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = dalloc(c, &cnt, (size_t)nchunks * sizeof(int));
+  if (e == cudaSuccess) e = dalloc(c, &off, (size_t)(nchunks + 1) * sizeof(int));
+  int nb_new = 0;
+  if (e == cudaSuccess) {
+    k_types<<<gcells, kBlock, 0, st>>>(d.flags, N, raw);
+    k_cc_init<<<gcells, kBlock, 0, st>>>(raw, N, lab);
+    c->ops.cc_union(raw, k, lab, st);
+    k_cc_compress<<<gcells, kBlock, 0, st>>>(N, lab);
+    k_cc_count<<<nchunks, kBlock, 0, st>>>(k, lab, cnt);
+    k_cc_scan<<<1, 1024, 0, st>>>(nchunks, cnt, off);
+    k_cc_number<<<nchunks, 32, 0, st>>>(k, lab, off, root_id);
+    c->ops.cc_assign(raw, k, lab, root_id, d.bid, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nb_new, off + nchunks, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(c, cnt);
+  dfree(c, off);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bubble relabelling");
+  const size_t W = (size_t)nb_new + 1;
+  if ((size_t)(nb_old > 0 ? nb_old : 1) * W > ((size_t)1 << 26))
+    return fail(c, FSLBM_ENOMEM, "bubble relabelling: too many bubbles for the overlap table");
+  long long *M = nullptr, *fr = nullptr;
+  const size_t nM = (size_t)(nb_old > 0 ? nb_old : 1) * W, nfr = (size_t)(nb_new > 0 ? nb_new : 1);
+  e = dalloc(c, &M, nM * sizeof(long long));
+  if (e == cudaSuccess) e = dalloc(c, &fr, nfr * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(M, 0, nM * sizeof(long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fr, 0, nfr * sizeof(long long), st);
+  if (e == cudaSuccess) {
+    k_bubble_overlap<<<gcells, kBlock, 0, st>>>(raw, d.phi, old_bid, d.bid, N, (int)W, M, fr);
+    e = cudaGetLastError();
+  }
+  std::vector<long long> hM(nM), hfr(nfr);
+  std::vector<double> V0_old((size_t)(nb_old > 0 ? nb_old : 1), 0.0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hM.data(), M, nM * sizeof(long long), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hfr.data(), fr, nfr * sizeof(long long), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && nb_old > 0)
+    e = cudaMemcpyAsync(V0_old.data(), d.V0, (size_t)nb_old * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(c, M);
+  dfree(c, fr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bubble relabelling");
+  std::vector<long long> row((size_t)(nb_old > 0 ? nb_old : 1), 0);
+  // the volume each old bubble hands on to new bubbles (column 0 excluded)
+  for (int A = 0; A < nb_old; ++A)
+    for (size_t j = 1; j < W; ++j) row[A] += hM[(size_t)A * W + j];
+  std::vector<double> V0_new(nfr, 0.0);
+  for (int C = 0; C < nb_new; ++C) {
+    double sum = 0.0;
+    for (int A = 0; A < nb_old; ++A) {
+      const long long m = hM[(size_t)A * W + (size_t)(C + 1)];
+      if (m == 0 || row[A] == 0) continue;
+      const double share = (double)m / (double)row[A];
+      const double part = V0_old[A] * share;
+      sum = sum + part;
+    }
+    const double free_part = (double)hfr[C] / 4294967296.0;
+    V0_new[C] = sum + free_part;
+  }
+  // per-bubble arrays for the new count (grown when it exceeds the capacity)
+  const bool grown = nb_new > c->nb_cap;
+  if (grown) {
+    dfree(c, d.V0);
+    dfree(c, d.pV);
+    dfree(c, d.gas_cnt);
+    dfree(c, d.iface_fix);
+    dfree(c, d.Vcur);
+    d.V0 = d.pV = d.Vcur = nullptr;
+    d.gas_cnt = d.iface_fix = nullptr;
+    const size_t cap = (size_t)nb_new * 2;
+    e = dalloc(c, &d.V0, cap * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, &d.pV, cap * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, &d.gas_cnt, cap * sizeof(long long));
+    if (e == cudaSuccess) e = dalloc(c, &d.iface_fix, cap * sizeof(long long));
+    if (e == cudaSuccess) e = dalloc(c, &d.Vcur, cap * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "bubble relabelling");
+    c->nb_cap = (int)cap;
+  }
+  if (nb_new > 0) {
+    e = cudaMemcpyAsync(d.V0, V0_new.data(), (size_t)nb_new * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.gas_cnt, 0, (size_t)nb_new * sizeof(long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.iface_fix, 0, (size_t)nb_new * sizeof(long long), st);
+    if (e == cudaSuccess) {
+      k_cc_volumes<<<gcells, kBlock, 0, st>>>(raw, d.phi, N, d.bid, d.gas_cnt, d.iface_fix);
+      k_relabel_pressure<<<(nb_new + 255) / 256, 256, 0, st>>>(nb_new, d.gas_cnt, d.iface_fix, d.V0, d.Vcur,
+                                                                d.pV, k.pv0);
+      e = cudaGetLastError();
+    }
+    // the host vectors must outlive the copy
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bubble relabelling");
+  }
+  d.nb = nb_new;
+  c->relabels += 1;
+  if (nb_new != nb_old || grown) {
+    e = build_graphs(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture after bubble relabelling");
+  }
+  return FSLBM_OK;
+}
+}  // namespace
+
 fslbm_status fslbm_step(fslbm_ctx* c, int n) {
   if (!c) return FSLBM_EINVAL;
   if (!c->initialized) return fail(c, FSLBM_ESTATE, "step before init");
@@ -600,6 +729,11 @@ fslbm_status fslbm_step(fslbm_ctx* c, int n) {
     c->launches += launches_per_step(c);
     c->parity ^= 1;
     c->step += 1;
+    const int K = c->prm.bubble_relabel_every;
+    if (K > 0 && c->kp.bubble_model && c->step % K == 0) {
+      const fslbm_status rs = relabel_bubbles(c);
+      if (rs != FSLBM_OK) return rs;
+    }
   }
   return FSLBM_OK;
 }
@@ -830,7 +964,8 @@ fslbm_status fslbm_load(fslbm_ctx* c, const void* buf, size_t size) {
   const size_t N = (size_t)c->kp.N;
   const size_t pdf_bytes = pdf_buffer_bytes(c->ops, c->q, c->kp.Np);
   if (std::memcmp(h.magic, "FSLBMCK2", 8) != 0 || h.nx != c->kp.nx || h.ny != c->kp.ny ||
-      h.nz != c->kp.nz || h.q != c->q || h.precision != c->prm.precision || h.nb != c->d.nb ||
+      h.nz != c->kp.nz || h.q != c->q || h.precision != c->prm.precision ||
+      (h.nb != c->d.nb && !c->kp.bubble_model) || h.nb < 0 ||
       h.pdf_bytes != (int64_t)pdf_bytes || h.ax[0] != c->kp.ax[0] || h.ax[1] != c->kp.ax[1] ||
       h.ax[2] != c->kp.ax[2])
     return fail(c, FSLBM_EINVAL, "checkpoint does not match this context");
@@ -840,6 +975,25 @@ fslbm_status fslbm_load(fslbm_ctx* c, const void* buf, size_t size) {
   if (size < need) return fail(c, FSLBM_EINVAL, "checkpoint truncated");
   const char* p = (const char*)buf + sizeof(h);
   cudaError_t e = cudaStreamSynchronize(c->stream);
+  // a run whose bubbles were relabelled may hold another bubble count
+  const bool nb_changed = (int)nb != c->d.nb;
+  const bool grown = e == cudaSuccess && (int)nb > c->nb_cap;
+  if (grown) {
+    dfree(c, c->d.V0);
+    dfree(c, c->d.pV);
+    dfree(c, c->d.gas_cnt);
+    dfree(c, c->d.iface_fix);
+    dfree(c, c->d.Vcur);
+    c->d.V0 = c->d.pV = c->d.Vcur = nullptr;
+    c->d.gas_cnt = c->d.iface_fix = nullptr;
+    e = dalloc(c, &c->d.V0, nb * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, &c->d.pV, nb * sizeof(double));
+    if (e == cudaSuccess) e = dalloc(c, &c->d.gas_cnt, nb * sizeof(long long));
+    if (e == cudaSuccess) e = dalloc(c, &c->d.iface_fix, nb * sizeof(long long));
+    if (e == cudaSuccess) e = dalloc(c, &c->d.Vcur, nb * sizeof(double));
+    if (e == cudaSuccess) c->nb_cap = (int)nb;
+  }
+  c->d.nb = (int)nb;
   auto h2d = [&](void* dst, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice);
     p += bytes;
@@ -875,6 +1029,10 @@ fslbm_status fslbm_load(fslbm_ctx* c, const void* buf, size_t size) {
   if (e != cudaSuccess) return cuda_fail(c, e, "fslbm_load");
   c->parity = 0;
   c->step = h.step;
+  if (nb_changed || grown) {
+    e = build_graphs(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture after fslbm_load");
+  }
   return FSLBM_OK;
 }
 

@@ -117,6 +117,8 @@ fslbm_status fslbm_batch_create(fslbm_ctx* const* members, int n, void* stream, 
     const fslbm_ctx* c = members[k];
     if (c->q != a->q || c->prm.precision != a->prm.precision || coll_of(c->kp) != coll_of(a->kp))
       return FSLBM_EINVAL;
+    // bubble relabelling runs between single-domain steps only
+    if (c->kp.bubble_model && c->prm.bubble_relabel_every > 0) return FSLBM_EINVAL;
   }
   fslbm_batch* b = new (std::nothrow) fslbm_batch();
   if (!b) return FSLBM_ENOMEM;

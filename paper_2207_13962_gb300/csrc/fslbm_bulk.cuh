@@ -57,7 +57,7 @@ __device__ __forceinline__ void bulk_cell(const DPtrs& d, const KParams& p, int 
   }
   bool bad = false;
   collide_any<Q, S, COLL>(f, p, bad);
-  store_cell<Q, S>(B, Np, c, f, s_in, bad);
+  store_cell<Q, S, true>(B, Np, c, f, s_in, bad);
   if (fl & F_NEAR_WALL) write_reflected<Q, S>(d, p, B, c, d.wallmask[c], general, f);
   if (bad) d.err[0] = 1;
 }

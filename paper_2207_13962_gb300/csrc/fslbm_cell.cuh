@@ -398,7 +398,24 @@ __device__ __forceinline__ float from_steps(long long n) {
 // the values the collision received, in grid steps: the rest deviation
 // becomes s_in minus the stored moving values (so the stored sum is s_in);
 // a rest outside the int32 range sets bad.
-template <int Q, class S>
+// A store that marks its line evict-first in the caches (the bulk sweep's
+// output is read again only next step, after the band kernels): 1 under
+// FSLBM_BULK_STCS, else a plain store.
+#ifndef FSLBM_BULK_STCS
+#define FSLBM_BULK_STCS 0
+#endif
+template <bool kStream, class T>
+__device__ __forceinline__ void st_pdf(T* p, T v) {
+  if constexpr (kStream && FSLBM_BULK_STCS != 0) {
+    if constexpr (sizeof(T) == 4) __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<unsigned int*>(&v));
+    else if constexpr (sizeof(T) == 2) __stcs(reinterpret_cast<unsigned short*>(p), *reinterpret_cast<unsigned short*>(&v));
+    else __stcs(reinterpret_cast<unsigned long long*>(p), *reinterpret_cast<unsigned long long*>(&v));
+  } else {
+    *p = v;
+  }
+}
+
+template <int Q, class S, bool kStream = false>
 __device__ __forceinline__ void store_cell(typename S::T* B, long long Np, long long c,
                                            const typename S::Real* f, long long s_in, bool& bad) {
   if constexpr (S::kExactRest) {
@@ -408,7 +425,7 @@ __device__ __forceinline__ void store_cell(typename S::T* B, long long Np, long 
     for (int i = 1; i < Q; ++i) {
       if (!(fabsf(f[i]) < kRange)) bad = true;
       const typename S::T v = S::stored(f[i]);
-      B[(long long)i * Np + c] = v;
+      st_pdf<kStream>(&B[(long long)i * Np + c], v);
       s_out += S::steps(v);
     }
     long long r = s_in - s_out;
@@ -416,12 +433,12 @@ __device__ __forceinline__ void store_cell(typename S::T* B, long long Np, long 
       bad = true;
       r = r > 0 ? 2147483647LL : -2147483647LL;
     }
-    rest_slice<Q, S>(B, Np)[c] = (int)r;
+    st_pdf<kStream>(&rest_slice<Q, S>(B, Np)[c], (int)r);
   } else {
     (void)s_in;
     (void)bad;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) B[(long long)i * Np + c] = store_w<S, Q>(f[i], i);
+    for (int i = 0; i < Q; ++i) st_pdf<kStream>(&B[(long long)i * Np + c], store_w<S, Q>(f[i], i));
   }
 }
 

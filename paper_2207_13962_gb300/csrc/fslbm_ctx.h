@@ -42,6 +42,8 @@ struct fslbm_ctx {
   bool ev_made = false;
   double stage_ms[fslbm::StageEvents::kStages] = {};
   long long launches = 0;
+  int nb_cap = 1;           // entries of the per-bubble arrays
+  long long relabels = 0;   // bubble relabellings done
   double* d_obs = nullptr;
   std::vector<void*> allocs;
   std::string err;

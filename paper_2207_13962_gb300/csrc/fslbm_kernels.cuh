@@ -301,6 +301,66 @@ static __global__ void k_cc_v0(int nb, const long long* gas_cnt, long long* ifac
   iface_fix[b] = 0;
 }
 
+// ------------------------------------------------- bubble relabelling
+// Coalescence and segmentation of bubbles between steps: the bubbles are
+// labelled again from the current flags (the kernels above), and the gas of
+// each old bubble goes to the new ones in proportion to the fixed-point
+// volume of its cells that each holds (the host combines the overlaps).
+
+// Cell types of the flags (the labelling kernels take bare types).
+static __global__ void k_types(const uint8_t* __restrict__ flags, int N, uint8_t* raw) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) raw[c] = flags[c] & F_TYPE;
+}
+
+// Overlap of old and new bubbles in 2^-32 fixed point: M[A * W + C + 1]
+// for a cell of old id A and new id C (column 0: no new bubble), fr[C] for
+// the cells of new bubble C that carried no id.  Integer sums, one atomic
+// per (old, new) pair present in a warp.
+static __global__ void k_bubble_overlap(const uint8_t* __restrict__ raw, const double* __restrict__ phi,
+                                        const int* __restrict__ old_bid, const int* __restrict__ bid, int N,
+                                        int W, long long* M, long long* fr) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  long long key = -1, v = 0;
+  if (c < N) {
+    const uint8_t t = raw[c];
+    if (t == T_GAS) v = 4294967296LL;
+    else if (t == T_IFACE) v = __double2ll_rn((1.0 - phi[c]) * 4294967296.0);
+    if (t == T_GAS || t == T_IFACE) {
+      const int A = old_bid[c], C = bid[c];
+      if (A >= 0) key = (long long)A * W + (C + 1);
+      else if (C >= 0) key = -2 - (long long)C;  // fr[C]
+    }
+  }
+  unsigned remaining = __ballot_sync(0xffffffffu, key != -1);
+  while (remaining) {
+    const int leader = __ffs(remaining) - 1;
+    const long long kk = __shfl_sync(0xffffffffu, key, leader);
+    const bool mine = key == kk;
+    long long sv = mine ? v : 0;
+    for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    if (lane == leader && sv) {
+      long long* dst = kk >= 0 ? &M[kk] : &fr[-2 - kk];
+      atomicAdd((unsigned long long*)dst, (unsigned long long)sv);
+    }
+    remaining &= ~__ballot_sync(0xffffffffu, mine);
+  }
+}
+
+// Volumes and pressures of the new bubbles (p^V = p^V(0) V0 / V, as in the
+// step's bubble update), with their gas reference V0 already set.
+static __global__ void k_relabel_pressure(int nb, const long long* gas_cnt, long long* iface_fix,
+                                          const double* V0, double* Vcur, double* pV, double pv0) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const long long acc = gas_cnt[b] * 4294967296LL + iface_fix[b];
+  const double V = __ll2double_rn(acc) / 4294967296.0;
+  pV[b] = (V > 0.0) ? (pv0 * V0[b]) / V : pv0;
+  Vcur[b] = V;
+  iface_fix[b] = 0;
+}
+
 // ------------------------------------------------------------- geometry
 // K8 weights (1 - r^2/4)^4 on the 3x3x3 block: r^2 = 0, 1, 2, 3.
 template <class R>

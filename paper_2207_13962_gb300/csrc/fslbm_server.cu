@@ -180,6 +180,8 @@ fslbm_status fslbm_server_submit(fslbm_server* s, const fslbm_request* rq, int64
   if (!s || !rq || !rq->fill || !rq->flags || rq->steps < 0) return FSLBM_EINVAL;
   if (rq->params.precision != s->cfg.precision)
     return sfail(s, FSLBM_EINVAL, "request precision differs from the server's");
+  if (rq->params.bubble_model && rq->params.bubble_relabel_every > 0)
+    return sfail(s, FSLBM_EINVAL, "bubble relabelling runs in single-domain contexts only");
   Req r;
   r.dom = rq->domain;
   r.variant = rq->bc_variant;

@@ -34,7 +34,7 @@ class fslbm_params(C.Structure):
     _fields_ = [("omega", C.c_double), ("trt_magic", C.c_double), ("g", C.c_double * 3),
                 ("sigma", C.c_double), ("eps_phi", C.c_double), ("p_v0", C.c_double),
                 ("precision", C.c_int), ("om3_fallback", C.c_int), ("bubble_model", C.c_int),
-                ("stream", C.c_void_p), ("smagorinsky_cs", C.c_double)]
+                ("stream", C.c_void_p), ("smagorinsky_cs", C.c_double), ("bubble_relabel_every", C.c_int)]
 
 
 class fslbm_tuning(C.Structure):
@@ -207,7 +207,7 @@ class Context:
     def __init__(self, shape, periodic=(False, False, False), q=19, collision="TRT", variant="OM",
                  precision="FP32", omega=1.0, trt_magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), sigma=0.0,
                  eps_phi=1e-2, p_v0=1.0 / 3.0, om3_fallback="NBKC", bubble_model=False,
-                 stream=None, axis_order=None, smagorinsky_cs=0.0):
+                 stream=None, axis_order=None, smagorinsky_cs=0.0, bubble_relabel_every=0):
         self.lib = load()
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -228,6 +228,7 @@ class Context:
         prm.bubble_model = int(bool(bubble_model))
         prm.stream = C.c_void_p(int(stream)) if stream else None
         prm.smagorinsky_cs = float(smagorinsky_cs)
+        prm.bubble_relabel_every = int(bubble_relabel_every)
         self.precision = prm.precision
         h = C.c_void_p()
         col = COLLISION[collision] if isinstance(collision, str) else int(collision)
@@ -426,7 +427,8 @@ def _params_for(sc, precision, **over):
     lib = load()
     kw = dict(omega=sc.omega, g=sc.g, sigma=sc.sigma, bubble_model=sc.bubble_model)
     kw.update({k: v for k, v in over.items() if k in ("omega", "g", "sigma", "bubble_model", "trt_magic",
-                                                      "eps_phi", "p_v0", "om3_fallback", "smagorinsky_cs")})
+                                                      "eps_phi", "p_v0", "om3_fallback", "smagorinsky_cs",
+                                                      "bubble_relabel_every")})
     prm = fslbm_params()
     lib.fslbm_params_default(C.byref(prm))
     prm.omega = float(kw["omega"])
@@ -440,6 +442,8 @@ def _params_for(sc, precision, **over):
         prm.om3_fallback = VARIANT[kw["om3_fallback"]]
     if "smagorinsky_cs" in kw:
         prm.smagorinsky_cs = float(kw["smagorinsky_cs"])
+    if "bubble_relabel_every" in kw:
+        prm.bubble_relabel_every = int(kw["bubble_relabel_every"])
     prm.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     return prm
 

@@ -297,6 +297,36 @@ def drop_impact(L=96, R_frac=0.12, depth_frac=0.1, U=0.03, g=1e-5, sigma=1e-4, n
                     meta=dict(L=L, R=R, depth=depth, U=U, g_abs=g, nu=nu))
 
 
+def bubble_pair(shape=(24, 16, 16), r=3.5, gap=0.3, U=0.05, sigma=1e-3, nu=0.02, q=19, variant="OM"):
+    """Two gas spheres of radius r in liquid (periodic box), their surfaces a
+    distance ``gap`` apart along x, pushed together by a liquid velocity
+    +-U along x (a Gaussian profile around their axis): the film between them
+    drains and the gas regions connect and part again (bubble coalescence and
+    segmentation), with the bubble model on."""
+    nx, ny, nz = shape
+    c1 = (nx / 2 - r - gap / 2, ny / 2, nz / 2)
+    c2 = (nx / 2 + r + gap / 2, ny / 2, nz / 2)
+
+    def inside(x, y, z):
+        d1 = (x - c1[0]) ** 2 + (y - c1[1]) ** 2 + (z - c1[2]) ** 2
+        d2 = (x - c2[0]) ** 2 + (y - c2[1]) ** 2 + (z - c2[2]) ** 2
+        return ~((d1 < r * r) | (d2 < r * r))
+
+    phi = _subsample_fraction(inside, (nx, ny, nz))
+    per = (True, True, True)
+    fill, flags = classify(phi, None, per, q)
+    N = nx * ny * nz
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    prof = np.exp(-((j + 0.5 - ny / 2) ** 2 + (k + 0.5 - nz / 2) ** 2) / 18.0)
+    ux = np.where(i + 0.5 < nx / 2, U, -U) * prof
+    vel = np.zeros(3 * N, np.float64)
+    live = (flags == LIQ) | (flags == IFACE)
+    vel[:N] = np.where(live, ux.reshape(-1), 0.0)
+    return Scenario("bubble_pair", (nx, ny, nz), per, fill, flags, vel, None, q=q, collision="TRT",
+                    variant=variant, omega=omega_from_nu(nu), sigma=sigma, bubble_model=True,
+                    meta=dict(r=r, gap=gap, U=U))
+
+
 def drop_requests(n=200, seed=13962, rate=20.0, lo=96, hi=256, **kw):
     """Poisson-arrival stream of drop-impact requests: list of
     (arrival_time_s, scenario kwargs) with seeded sizes and parameters."""
