@@ -470,14 +470,13 @@ def _crown(fill, flags, L):
     return float(top + f3[top][flags.reshape(L, L, L)[top] == S.IFACE].max())
 
 
-def _lifted(fill, sc):
+def _lifted(fill, L, depth):
     """Drop impact: liquid volume above the undisturbed pool, the sum of the
     fill level over the layers k >= depth + 2 (the drop's remnant and the
     crown sheet).  An integral of the fill level, so it moves by about the
     size of the fill levels' own error, unlike the crown height, which jumps
     by a cell when one interface cell at the tip appears or empties."""
-    L = sc.shape[0]
-    k0 = int(np.ceil(sc.meta["depth"])) + 2
+    k0 = int(np.ceil(depth)) + 2
     return float(fill.reshape(L, L, L)[k0:].sum())
 
 
@@ -558,112 +557,135 @@ def bench_batch(args, emit=True):
     return out
 
 
-def _serve_trace(scs, steps, submit_fn, poll_fn):
-    """Replays an arrival trace in real time through a server; returns the
-    results by trace index and the makespan (first arrival to last result)."""
-    pending = list(range(len(scs)))
-    ids, results = {}, {}
+def _compact_drop(kw):
+    from paper_2207_13962_gb300 import scenarios as S
+    return S.drop_impact_compact(**kw)
+
+
+def _drop_states(trace):
+    """Compact initial states of a request trace, built by a spawned process
+    pool (before any CUDA call of this process)."""
+    import multiprocessing as mp
+    kws = [kw for _, kw in trace]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1, len(kws)))) as pool:
+        return pool.map(_compact_drop, kws, chunksize=1)
+
+
+def _replay(arrivals, step_fn):
+    """Replays arrival times (seconds, sorted) in real time.  step_fn(ready)
+    gets the arrived requests that have not started (it removes those it
+    starts) and returns (finished [(k, result)], busy).  Time-to-result runs
+    from a request's arrival to its result on the host.  Returns the results
+    by trace index and the makespan (trace start to the last result)."""
+    n, nxt, ready, results = len(arrivals), 0, [], {}
     t0 = time.perf_counter()
-    while len(results) < len(scs):
+    while len(results) < n:
         now = time.perf_counter() - t0
-        while pending and scs[pending[0]][0] <= now:
-            k = pending.pop(0)
-            ids[submit_fn(scs[k][1], steps)] = k
-        if not ids and pending:
-            time.sleep(max(0.0, scs[pending[0]][0] - (time.perf_counter() - t0)))
-            continue
-        for rid, r in poll_fn():
-            results[ids.pop(rid)] = r
+        while nxt < n and arrivals[nxt] <= now:
+            ready.append(nxt)
+            nxt += 1
+        done, busy = step_fn(ready)
+        t = time.perf_counter() - t0
+        for k, r in done:
+            r["ttr"] = t - arrivals[k]
+            results[k] = r
+        if not busy and not ready and nxt < n:
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
     return results, time.perf_counter() - t0
 
 
 def bench_serve(args, emit=True):
-    """Drop impacts arriving as a Poisson stream (mean 20 req/s, seeded sizes
-    96..256), replayed in real time: a FIFO server that runs each request
-    alone in plain FP32, one after another, against the continuous-batching
-    server in FP32 and in the reduced (by default mass-conserving FP16)
-    storage.  Time-to-result runs from a request's arrival to its result on
-    the host; the crown-height error is relative to the plain FP32 run."""
+    """Drop impacts arriving as a Poisson stream (seeded sizes 96..256),
+    replayed in real time: a FIFO server that runs each request alone in
+    plain FP32, one after another, against the continuous-batching server in
+    FP32 and in the reduced storage formats.  Requests wait on the host in
+    compact form (cell types and interface fill levels) and are expanded to
+    full host arrays when they start (FIFO) or when the server's own queue
+    has room (at most --max-active waiting there), so a long trace holds
+    about one byte per cell on the host.  Time-to-result runs from a
+    request's arrival to its result on the host; the observables are
+    relative to the plain FP32 run."""
+    from paper_2207_13962_gb300 import scenarios as S
+    trace = S.drop_requests(n=args.requests, rate=args.rate)
+    comp = _drop_states(trace)  # before the first CUDA call: the pool is spawned
     import torch
     from paper_2207_13962_gb300 import fslbm
-    from paper_2207_13962_gb300 import scenarios as S
     torch.cuda.set_device(0)
-    trace = S.drop_requests(n=args.requests, rate=args.rate)
-    scs = [(t, S.drop_impact(**kw)) for t, kw in trace]
+    arrivals = [t for t, _ in trace]
     steps = args.serve_steps
-    cells = sum(sc.N for _, sc in scs)
+    cells = sum(c.N for c in comp)
     out = {}
 
+    def observe(k, fill, flags):
+        return {"crown": _crown(fill, flags, comp[k].shape[0]),
+                "lifted": _lifted(fill, comp[k].shape[0], comp[k].depth)}
+
     # FIFO, one at a time, plain FP32 contexts
-    queue = []
-    next_id = [0]
+    def fifo_step(ready):
+        if not ready:
+            return [], False
+        k = ready.pop(0)
+        c = fslbm.context_for(comp[k].expand(), precision="FP32")
+        M0 = c.observables()["total_mass"]
+        c.step(steps)
+        c.sync()
+        r = c.read(pdf=False)
+        obs = c.observables()
+        c.close()
+        return [(k, {**observe(k, r["fill"], r["flags"]), "status": obs["status"],
+                     "drift": abs(obs["total_mass"] - M0) / M0})], True
 
-    def fifo_submit(sc, n):
-        next_id[0] += 1
-        queue.append((next_id[0], sc, time.perf_counter()))
-        return next_id[0]
-
-    def fifo_poll():
-        done = []
-        while queue and not done:
-            k, sc, t_sub = queue.pop(0)
-            c = fslbm.context_for(sc, precision="FP32")
-            M0 = c.observables()["total_mass"]
-            c.step(steps)
-            c.sync()
-            r = c.read(pdf=False)
-            obs = c.observables()
-            c.close()
-            done.append((k, {"t_result": time.perf_counter() - t_sub, "fill": r["fill"], "flags": r["flags"],
-                             "drift": abs(obs["total_mass"] - M0) / M0}))
-        return done
-
-    res, makespan = _serve_trace(scs, steps, fifo_submit, fifo_poll)
-    ref = [_crown(res[k]["fill"], res[k]["flags"], scs[k][1].shape[0]) for k in range(len(scs))]
-    ref_v = [_lifted(res[k]["fill"], scs[k][1]) for k in range(len(scs))]
-    ttr = [res[k]["t_result"] for k in range(len(scs))]
+    res, makespan = _replay(arrivals, fifo_step)
+    ref = res
+    ttr = [res[k]["ttr"] for k in range(len(comp))]
+    stable_ref = {k for k in res if res[k]["status"] == 0}
     out["plain_fp32_fifo"] = {"mlups": round(cells * steps / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
                               "p50_s": round(float(np.percentile(ttr, 50)), 4),
                               "p99_s": round(float(np.percentile(ttr, 99)), 4),
-                              "mass_drift_rel_max": max(res[k]["drift"] for k in res)}
-    for prec in ["FP32"] + [p for p in args.batch_precision.split(",") if p != "FP32"]:
+                              "unstable_runs": sorted(set(res) - stable_ref),
+                              "mass_drift_rel_max_stable": max((res[k]["drift"] for k in stable_ref), default=None)}
+    arms = [] if args.skip_served_fp32 else ["FP32"]
+    for prec in arms + [p for p in args.batch_precision.split(",") if p != "FP32"]:
         srv = fslbm.Server(q=19, precision=prec, max_active=args.max_active, chunk_steps=args.chunk_steps)
-        m0 = {}
+        live = {}
 
-        def submit(sc, n):
-            rid = srv.submit(sc, n)
-            m0[rid] = None
-            return rid
-
-        def poll():
+        def serve_step(ready):
+            while ready and srv.stats()["queued"] < args.max_active:
+                k = ready.pop(0)
+                live[srv.submit(comp[k].expand(), steps)] = k
+            if not live:
+                return [], False
             srv.poll()
             got = []
-            for rid in list(m0):
+            for rid in list(live):
                 r = srv.result(rid)
                 if r is not None:
-                    del m0[rid]
-                    got.append((rid, r))
-            return got
+                    k = live.pop(rid)
+                    got.append((k, {**observe(k, r["fill"], r["flags"]), "status": r["status"]}))
+            return got, True
 
-        res, makespan = _serve_trace(scs, steps, submit, poll)
-        ttr = [res[k]["t_result"] for k in range(len(scs))]
-        err = max(abs(_crown(res[k]["fill"], res[k]["flags"], scs[k][1].shape[0]) - ref[k]) / max(ref[k], 1e-30)
-                  for k in range(len(scs)))
-        err_v = max(abs(_lifted(res[k]["fill"], scs[k][1]) - ref_v[k]) / max(ref_v[k], 1e-30)
-                    for k in range(len(scs)))
+        res, makespan = _replay(arrivals, serve_step)
+        ttr = [res[k]["ttr"] for k in range(len(comp))]
+        both = sorted(k for k in stable_ref if res[k]["status"] == 0)  # stable alone and served
+        rel = lambda key: max((abs(res[k][key] - ref[k][key]) / max(abs(ref[k][key]), 1e-30) for k in both),
+                              default=None)
         st = srv.stats()
         out[f"served_{prec.lower()}"] = {
             "mlups": round(cells * steps / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
             "p50_s": round(float(np.percentile(ttr, 50)), 4), "p99_s": round(float(np.percentile(ttr, 99)), 4),
-            "crown_rel_err_vs_plain_fp32": err, "lifted_volume_rel_err_vs_plain_fp32": err_v,
+            "unstable_runs": sorted(k for k in res if res[k]["status"] != 0), "compared_runs": len(both),
+            "crown_rel_err_vs_plain_fp32": rel("crown"), "lifted_volume_rel_err_vs_plain_fp32": rel("lifted"),
             "max_active_seen": st["max_active_seen"],
             "batch_rebuilds": st["batch_rebuilds"]}
         srv.close()
-    summary = {"workload": f"{len(scs)} drop impacts of seeded sides {min(sc.shape[0] for _, sc in scs)}.."
-                           f"{max(sc.shape[0] for _, sc in scs)} (seed 13962), Poisson arrivals {args.rate}/s, "
-                           f"{steps} steps each, D3Q19 TRT OM, replayed in real time",
+    sides = [c.shape[0] for c in comp]
+    summary = {"workload": f"{len(comp)} drop impacts of seeded sides {min(sides)}..{max(sides)} (seed 13962), "
+                           f"Poisson arrivals {args.rate}/s, {steps} steps each, D3Q19 TRT OM, replayed in real time",
                "cells": cells, "unit": "MLUPS", "results": out, "max_active": args.max_active,
                "chunk_steps": args.chunk_steps,
+               "time_to_result": "from the request's arrival to its result on the host",
+               "errors": "over the runs that stayed stable (status 0) alone and served; unstable_runs lists the "
+                         "trace indices that ended with FSLBM_EUNSTABLE",
                "observable": "crown height max over interface cells of (k + fill), and the liquid volume above "
                              "the pool (sum of the fill level over layers k >= depth + 2), each relative to the "
                              "plain FP32 run"}
@@ -903,6 +925,8 @@ def main(argv=None):
     ap.add_argument("--serve-steps", type=int, default=1000, help="serve_drops: steps per request")
     ap.add_argument("--max-active", type=int, default=16, help="serve_drops: resident runs")
     ap.add_argument("--chunk-steps", type=int, default=100, help="serve_drops: steps per round")
+    ap.add_argument("--skip-served-fp32", action="store_true",
+                    help="serve_drops: serve only the --batch-precision formats (the FIFO FP32 arm still runs)")
     args = ap.parse_args(argv)
     if args.sector_census:
         print(json.dumps(sector_census(args.workload, args.variant)))

@@ -267,11 +267,8 @@ def taylor_bubble(nx=160, ny=160, nz=1024, D=128, bubble_d=96, bubble_len=256, z
                     meta=dict(D=D, bubble_d=bubble_d, bubble_len=bubble_len, g_abs=g, nu=nu))
 
 
-def drop_impact(L=96, R_frac=0.12, depth_frac=0.1, U=0.03, g=1e-5, sigma=1e-4, nu=1e-3,
-                variant="OM", q=19, collision="TRT", steps=5000):
-    """Drop onto a thin pool: L^3 cube, periodic x/y, no-slip z; pool depth
-    depth_frac*L; sphere of radius R_frac*L centred at height pool + R + 1
-    moving with velocity -U along z."""
+def _drop_geometry(L, R_frac, depth_frac, q):
+    """Fill levels and cell types of a drop above a thin pool in an L^3 cube."""
     nx = ny = nz = int(L)
     depth = depth_frac * L
     R = R_frac * L
@@ -282,19 +279,72 @@ def drop_impact(L=96, R_frac=0.12, depth_frac=0.1, U=0.03, g=1e-5, sigma=1e-4, n
         return (((x - c) ** 2 + (y - c) ** 2 + (z - zc) ** 2) < R * R) | (z < depth)
 
     phi = _subsample_fraction(inside, (nx, ny, nz))
-    periodic = (True, True, False)
-    fill, flags = classify(phi, None, periodic, q)
-    rho = hydrostatic((nx, ny, nz), 2, g, depth, flags)
-    # the drop keeps rho = 1 (it is above the pool surface)
-    k = np.repeat(np.arange(nz), nx * ny)
-    rho = np.where(k + 0.5 > depth + 1.0, np.where(rho > 0, 1.0, rho), rho)
+    return classify(phi, None, (True, True, False), q)
+
+
+def _drop_state(fill, flags, L, R_frac, depth_frac, U, g, sigma, nu, variant, q, collision, steps):
+    """Scenario of a drop impact from its fill levels and cell types: the pool
+    hydrostatic below depth + 1 (rho = 1 + 3 g (depth - z)), the drop at
+    rho = 1 moving with -U along z."""
+    nx = ny = nz = int(L)
+    depth = depth_frac * L
+    R = R_frac * L
+    fluid = (flags == LIQ) | (flags == IFACE)
+    zc = np.arange(nz, dtype=np.float64) + 0.5
+    above = np.repeat(zc > depth + 1.0, nx * ny)
+    rho_layer = np.repeat(1.0 + 3.0 * g * (depth - zc), nx * ny)
+    rho = np.where(fluid & ~above, rho_layer, 1.0)
     vel = np.zeros(3 * nx * ny * nz, np.float64)
-    in_drop = (k + 0.5 > depth + 1.0) & ((flags == LIQ) | (flags == IFACE))
-    vel[2 * nx * ny * nz:][in_drop] = -U
-    return Scenario("drop_impact", (nx, ny, nz), periodic, fill, flags, vel, rho, q=q,
+    vel[2 * nx * ny * nz:][above & fluid] = -U
+    return Scenario("drop_impact", (nx, ny, nz), (True, True, False), fill, flags, vel, rho, q=q,
                     collision=collision, variant=variant, omega=omega_from_nu(nu),
                     g=(0.0, 0.0, -g), sigma=sigma, steps=steps,
                     meta=dict(L=L, R=R, depth=depth, U=U, g_abs=g, nu=nu))
+
+
+def drop_impact(L=96, R_frac=0.12, depth_frac=0.1, U=0.03, g=1e-5, sigma=1e-4, nu=1e-3,
+                variant="OM", q=19, collision="TRT", steps=5000):
+    """Drop onto a thin pool: L^3 cube, periodic x/y, no-slip z; pool depth
+    depth_frac*L; sphere of radius R_frac*L centred at height pool + R + 1
+    moving with velocity -U along z."""
+    fill, flags = _drop_geometry(L, R_frac, depth_frac, q)
+    return _drop_state(fill, flags, L, R_frac, depth_frac, U, g, sigma, nu, variant, q, collision, steps)
+
+
+@dataclass
+class CompactDrop:
+    """A drop-impact initial state held as its cell types and the fill levels
+    of its interface cells (about one byte per cell, against ~80 for the full
+    host arrays); expand() rebuilds exactly the arrays of drop_impact()."""
+    kw: dict
+    flags: np.ndarray
+    iface_fill: np.ndarray
+
+    @property
+    def shape(self):
+        return (int(self.kw["L"]),) * 3
+
+    @property
+    def N(self):
+        return int(self.flags.size)
+
+    @property
+    def depth(self):
+        return self.kw["depth_frac"] * self.kw["L"]
+
+    def expand(self) -> Scenario:
+        fill = (self.flags == LIQ).astype(np.float64)
+        fill[self.flags == IFACE] = self.iface_fill
+        return _drop_state(fill, self.flags, **self.kw)
+
+
+def drop_impact_compact(L=96, R_frac=0.12, depth_frac=0.1, U=0.03, g=1e-5, sigma=1e-4, nu=1e-3,
+                        variant="OM", q=19, collision="TRT", steps=5000) -> CompactDrop:
+    """drop_impact() in compact form (for request streams held on the host)."""
+    fill, flags = _drop_geometry(L, R_frac, depth_frac, q)
+    kw = dict(L=L, R_frac=R_frac, depth_frac=depth_frac, U=U, g=g, sigma=sigma, nu=nu, variant=variant, q=q,
+              collision=collision, steps=steps)
+    return CompactDrop(kw, flags, fill[flags == IFACE].copy())
 
 
 def bubble_pair(shape=(24, 16, 16), r=3.5, gap=0.3, U=0.05, sigma=1e-3, nu=0.02, q=19, variant="OM"):

@@ -93,3 +93,17 @@ def test_sector_census_bounds():
     assert distinct <= c["warp_sector_requests"]
     assert distinct <= c["read_sectors_64B_chunks"] <= c["read_sectors_128B_lines"]
     assert c["partial_write_sectors"] >= 0 and c["reflected_write_sectors"] >= 0
+
+
+def test_compact_drop_expands_to_the_full_arrays():
+    """The request stream holds drop impacts as cell types plus interface
+    fill levels; expanding them must give exactly the generator's arrays."""
+    for kw in (dict(L=33, R_frac=0.14, U=0.045), dict(L=48, R_frac=0.08, U=0.02)):
+        full = S.drop_impact(**kw)
+        comp = S.drop_impact_compact(**kw)
+        assert comp.flags.nbytes + comp.iface_fill.nbytes < 2 * comp.N
+        back = comp.expand()
+        for a, b in ((full.fill, back.fill), (full.flags, back.flags), (full.velocity, back.velocity),
+                     (full.density, back.density)):
+            np.testing.assert_array_equal(a, b)
+        assert back.meta == full.meta and back.shape == full.shape
