@@ -594,15 +594,45 @@ def _replay(arrivals, step_fn):
     return results, time.perf_counter() - t0
 
 
+class _Expander:
+    """Expands compact requests into full host arrays on worker threads, a
+    few requests ahead of the ones being started, so that the host loop keeps
+    the GPU fed meanwhile (the server's poll and the steps release the
+    interpreter).  Both servers of the comparison use it."""
+
+    def __init__(self, comp, ahead):
+        import concurrent.futures as cf
+        self.comp, self.ahead = comp, ahead
+        self.pool = cf.ThreadPoolExecutor(max_workers=2)
+        self.fut = {}
+
+    def prefetch(self, ready):
+        for k in ready[:self.ahead]:
+            if k not in self.fut:
+                self.fut[k] = self.pool.submit(self.comp[k].expand)
+
+    def done(self, k):
+        return k in self.fut and self.fut[k].done()
+
+    def take(self, k):
+        if k not in self.fut:
+            self.fut[k] = self.pool.submit(self.comp[k].expand)
+        return self.fut.pop(k).result()
+
+    def close(self):
+        self.pool.shutdown()
+
+
 def bench_serve(args, emit=True):
     """Drop impacts arriving as a Poisson stream (seeded sizes 96..256),
     replayed in real time: a FIFO server that runs each request alone in
     plain FP32, one after another, against the continuous-batching server in
     FP32 and in the reduced storage formats.  Requests wait on the host in
-    compact form (cell types and interface fill levels) and are expanded to
-    full host arrays when they start (FIFO) or when the server's own queue
-    has room (at most --max-active waiting there), so a long trace holds
-    about one byte per cell on the host.  Time-to-result runs from a
+    compact form (cell types and interface fill levels); worker threads
+    expand the next few of them to full host arrays while the GPU runs, and
+    a request is handed over when it starts (FIFO) or when the server's own
+    queue has room (at most --max-active waiting there), so a long trace
+    holds about one byte per cell on the host.  Time-to-result runs from a
     request's arrival to its result on the host; the observables are
     relative to the plain FP32 run."""
     from paper_2207_13962_gb300 import scenarios as S
@@ -615,17 +645,21 @@ def bench_serve(args, emit=True):
     steps = args.serve_steps
     cells = sum(c.N for c in comp)
     out = {}
+    les = {"smagorinsky_cs": args.serve_cs} if args.serve_cs > 0 else {}
 
     def observe(k, fill, flags):
         return {"crown": _crown(fill, flags, comp[k].shape[0]),
                 "lifted": _lifted(fill, comp[k].shape[0], comp[k].depth)}
 
     # FIFO, one at a time, plain FP32 contexts
+    exp = _Expander(comp, 2)
+
     def fifo_step(ready):
+        exp.prefetch(ready)
         if not ready:
             return [], False
         k = ready.pop(0)
-        c = fslbm.context_for(comp[k].expand(), precision="FP32")
+        c = fslbm.context_for(exp.take(k), precision="FP32", **les)
         M0 = c.observables()["total_mass"]
         c.step(steps)
         c.sync()
@@ -636,6 +670,7 @@ def bench_serve(args, emit=True):
                      "drift": abs(obs["total_mass"] - M0) / M0})], True
 
     res, makespan = _replay(arrivals, fifo_step)
+    exp.close()
     ref = res
     ttr = [res[k]["ttr"] for k in range(len(comp))]
     stable_ref = {k for k in res if res[k]["status"] == 0}
@@ -648,13 +683,18 @@ def bench_serve(args, emit=True):
     for prec in arms + [p for p in args.batch_precision.split(",") if p != "FP32"]:
         srv = fslbm.Server(q=19, precision=prec, max_active=args.max_active, chunk_steps=args.chunk_steps)
         live = {}
+        exp = _Expander(comp, 4)
 
         def serve_step(ready):
-            while ready and srv.stats()["queued"] < args.max_active:
+            exp.prefetch(ready)
+            while ready and exp.done(ready[0]) and srv.stats()["queued"] < args.max_active:
                 k = ready.pop(0)
-                live[srv.submit(comp[k].expand(), steps)] = k
+                live[srv.submit(exp.take(k), steps, **les)] = k
             if not live:
-                return [], False
+                if not ready:
+                    return [], False
+                k = ready.pop(0)  # nothing on the GPU: wait for this expansion
+                live[srv.submit(exp.take(k), steps, **les)] = k
             srv.poll()
             got = []
             for rid in list(live):
@@ -665,6 +705,7 @@ def bench_serve(args, emit=True):
             return got, True
 
         res, makespan = _replay(arrivals, serve_step)
+        exp.close()
         ttr = [res[k]["ttr"] for k in range(len(comp))]
         both = sorted(k for k in stable_ref if res[k]["status"] == 0)  # stable alone and served
         rel = lambda key: max((abs(res[k][key] - ref[k][key]) / max(abs(ref[k][key]), 1e-30) for k in both),
@@ -680,7 +721,8 @@ def bench_serve(args, emit=True):
         srv.close()
     sides = [c.shape[0] for c in comp]
     summary = {"workload": f"{len(comp)} drop impacts of seeded sides {min(sides)}..{max(sides)} (seed 13962), "
-                           f"Poisson arrivals {args.rate}/s, {steps} steps each, D3Q19 TRT OM, replayed in real time",
+                           f"Poisson arrivals {args.rate}/s, {steps} steps each, D3Q19 TRT OM"
+                           + (f", Smagorinsky C_S {args.serve_cs}" if args.serve_cs > 0 else "") + ", replayed in real time",
                "cells": cells, "unit": "MLUPS", "results": out, "max_active": args.max_active,
                "chunk_steps": args.chunk_steps,
                "time_to_result": "from the request's arrival to its result on the host",
@@ -790,8 +832,8 @@ def taylor_rise(args):
     zc_of = np.arange(nz, dtype=np.float64)[:, None, None] + 0.5
     steps, every = args.rise_steps, 1000
     out = {}
-    for prec, scn in (("FP64", sc), ("FP64_perturbed", _perturbed(sc)), ("FP32", sc), ("FP32MC", sc),
-                      ("FP16SMC", sc)):
+    for prec, scn in (("FP64", sc), ("FP64_perturbed", _perturbed(sc)), ("FP64_perturbed_2", _perturbed(sc, seed=2)),
+                      ("FP32", sc), ("FP32MC", sc), ("FP16SMC", sc)):
         c = fslbm.context_for(scn, precision=prec.split("_")[0])
         M0 = c.observables()["total_mass"]
         t, z, t0 = [], [], time.perf_counter()
@@ -809,11 +851,13 @@ def taylor_rise(args):
         vel = float(np.polyfit(t[-q:], z[-q:], 1)[0])
         out[prec] = {"rise_velocity": vel, "centroid_final": z[-1], "status": obs["status"],
                      "mass_drift_rel": abs(obs["total_mass"] - M0) / M0, "seconds": round(time.perf_counter() - t0, 1)}
-    for prec in ("FP64_perturbed", "FP32", "FP32MC", "FP16SMC"):
+    for prec in ("FP64_perturbed", "FP64_perturbed_2", "FP32", "FP32MC", "FP16SMC"):
         out[prec]["rise_velocity_rel_err_vs_fp64"] = abs(out[prec]["rise_velocity"] - out["FP64"]["rise_velocity"]) / \
             abs(out["FP64"]["rise_velocity"])
     line = {"metric": METRIC, "workload": f"Taylor bubble rise velocity, {steps} steps", "results": out,
-            "floor": "FP64_perturbed: the FP64 run from interface fill levels moved by a seeded +-1e-7",
+            "floor": "FP64_perturbed(_2): the FP64 run from interface fill levels moved by a seeded +-1e-7 "
+                     "(two seeds: whether a perturbation this small flips a conversion decision depends on where "
+                     "it falls)",
             "data": "synthetic (seeded generator, no dataset)"}
     print(json.dumps(line), flush=True)
     return line
@@ -925,6 +969,8 @@ def main(argv=None):
     ap.add_argument("--serve-steps", type=int, default=1000, help="serve_drops: steps per request")
     ap.add_argument("--max-active", type=int, default=16, help="serve_drops: resident runs")
     ap.add_argument("--chunk-steps", type=int, default=100, help="serve_drops: steps per round")
+    ap.add_argument("--serve-cs", type=float, default=0.0,
+                    help="serve_drops: Smagorinsky constant of the drop impacts (0: no turbulence model)")
     ap.add_argument("--skip-served-fp32", action="store_true",
                     help="serve_drops: serve only the --batch-precision formats (the FIFO FP32 arm still runs)")
     args = ap.parse_args(argv)

@@ -248,7 +248,9 @@ fslbm_status fslbm_bubbles(fslbm_ctx* ctx, double* volume, double* pressure,
 fslbm_status fslbm_set_timing(fslbm_ctx* ctx, int enable);
 /* Accumulated milliseconds per stage since timing was enabled, one stage per
  * kernel of the step in the order geometry, bulk, interface, resolve, count,
- * apply, finalize, bubbles; writes min(cap, 8) values. */
+ * apply, finalize (with the rebuild of the interface list in cell order),
+ * bubbles; writes min(cap, 8) values.  The FP32 and 16-bit engines run the
+ * geometry inside the bulk launch, so their geometry stage is empty. */
 fslbm_status fslbm_stage_times(fslbm_ctx* ctx, double* ms, int cap, int* n_launches);
 
 /* Checkpoint of the full state (PDFs, flags, fill, mass, bubbles, step) into

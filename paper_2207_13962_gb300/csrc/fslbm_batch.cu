@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "fslbm_band_list.cuh"
 #include "fslbm_ctx.h"
 
 using namespace fslbm;
@@ -22,6 +23,9 @@ struct fslbm_batch {
   std::vector<cudaEvent_t> mev;    // one per member: its stream's latest work
   DomRec* d_recs = nullptr;
   int* d_off = nullptr;
+  int* d_chunk = nullptr;          // prefix of the members' interface-list chunks (n + 1)
+  int* d_cnt = nullptr;            // their list counters of kb_compact_band (n)
+  int nchunks = 0;
   BatchPlan plan{};
   std::vector<DomRec> h_recs;
   cudaGraphExec_t graph = nullptr;
@@ -59,6 +63,11 @@ cudaError_t capture(fslbm_batch* b) {
   if (e != cudaSuccess) return e;
   b->ops.batch_step(b->d_recs, b->plan, b->sms * b->tune.band_blocks_per_sm,
                     b->sms * b->tune.bulk_blocks_per_sm, b->collision, b->cap, &b->fork);
+  // every member's next interface list rewritten in cell order
+  const int n = (int)b->m.size();
+  cudaMemsetAsync(b->d_cnt, 0, (size_t)n * sizeof(int), b->cap);
+  kb_compact_band<<<b->nchunks < 8 * b->sms ? b->nchunks : 8 * b->sms, kBlock, 0, b->cap>>>(
+      b->d_recs, b->d_chunk, n, b->d_cnt);
   e = cudaStreamEndCapture(b->cap, &g);
   if (e != cudaSuccess) return e;
   e = prioritise_nodes(g, b->ops.batch_bulk_fn[b->collision], nullptr);
@@ -141,6 +150,16 @@ fslbm_status fslbm_batch_create(fslbm_ctx* const* members, int n, void* stream, 
   // four prefix arrays of n + 1 entries, then the bulk sweep's hand-out
   // counter and the fused sweep's tile counter
   if (e == cudaSuccess) e = cudaMalloc(&b->d_off, (4 * (size_t)(n + 1) + 2) * sizeof(int));
+  if (e == cudaSuccess) {
+    // interface-list chunks of each member: fixed by its cell count
+    std::vector<int> off((size_t)n + 1, 0);
+    for (int k = 0; k < n; ++k) off[k + 1] = off[k] + (members[k]->kp.N + kCompactChunk - 1) / kCompactChunk;
+    b->nchunks = off[n];
+    e = cudaMalloc(&b->d_chunk, ((size_t)n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_cnt, (size_t)n * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_chunk, off.data(), ((size_t)n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->fork.side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork.fork, cudaEventDisableTiming);
@@ -265,6 +284,8 @@ void fslbm_batch_destroy(fslbm_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->d_recs) cudaFree(b->d_recs);
   if (b->d_off) cudaFree(b->d_off);
+  if (b->d_chunk) cudaFree(b->d_chunk);
+  if (b->d_cnt) cudaFree(b->d_cnt);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->fork.side) cudaStreamDestroy(b->fork.side);
   if (b->fork.fork) cudaEventDestroy(b->fork.fork);

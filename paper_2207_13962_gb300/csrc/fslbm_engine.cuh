@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "fslbm_kernels.cuh"
+#include "fslbm_band_list.cuh"
 
 namespace fslbm {
 
@@ -39,6 +40,13 @@ struct Engine {
     return sizeof(typename S::Real) == 4 ? kBulkMinBlocks32 : 2;
   }
   static int grid_cells(const KParams& p) { return (p.N + kBlock - 1) / kBlock; }
+  // blocks of k_compact_band: one chunk of kCompactChunk cells each, at most
+  // 4 per band block (8 per SM; the grid loops over the remaining chunks)
+  static int compact_grid(const KParams& p, int band_grid) {
+    const long long chunks = ((long long)p.N + kCompactChunk - 1) / kCompactChunk;
+    const long long cap = 4LL * band_grid;
+    return (int)(chunks < cap ? chunks : cap);
+  }
   // the FP32 and 16-bit engines fold the geometry pass into the bulk sweep
   static constexpr bool kFusedGeo = sizeof(typename S::Real) == 4 && !kTmaBulk;
   // shared-memory carveout (percent of the 228 KB) that holds a tile buffer
@@ -91,6 +99,7 @@ struct Engine {
       k_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
       if (ev) ev->mark(6, st);
       k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
+      k_compact_band<<<compact_grid(p, band_grid), kBlock, 0, st>>>(d, p, parity);
       if (ev) ev->mark(7, st);
       if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
       if (ev) ev->mark(8, st);
@@ -133,6 +142,7 @@ struct Engine {
     k_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
     if (ev) ev->mark(6, st);
     k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
+    k_compact_band<<<compact_grid(p, band_grid), kBlock, 0, st>>>(d, p, parity);
     if (ev) ev->mark(7, st);
     if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
     if (ev) ev->mark(8, st);
@@ -242,13 +252,13 @@ struct Engine {
       o.bulk_fn[7] = (const void*)&k_bulk<Q, S, 7>;
     }
     o.bulk_blocks_per_sm = bulk_blocks_per_sm();
-    o.step_launches = kFusedGeo ? 6 : 7;
+    o.step_launches = kFusedGeo ? 7 : 8;
     o.bulk_smem = kTmaBulk ? tma_smem<Q, typename S::T>() : kFusedGeo ? geometry_smem<typename S::Real>() : 0;
     o.batch_step = &batch_step;
     // two plan kernels, geometry, bulk sweep, interface update, resolve,
     // count, apply, finalize, bubbles + buffer swap (one less when the
     // geometry is folded into the sweep)
-    o.batch_step_launches = kFusedGeo ? 9 : 10;
+    o.batch_step_launches = kFusedGeo ? 10 : 11;  // with kb_compact_band, launched by the batch
     if constexpr (kFusedGeo) {
       const void* fns[8] = {(const void*)&kb_bulk_geo<Q, S, 0>, (const void*)&kb_bulk_geo<Q, S, 1>,
                             (const void*)&kb_bulk_geo<Q, S, 2>, (const void*)&kb_bulk_geo<Q, S, 3>,

@@ -1476,7 +1476,10 @@ static __global__ void k_tiles_of_band(DPtrs d, KParams p, int parity) {
 
 // Final flags, next interface list, bubble gas counts and interface sums.
 // Entries [base, base + 32) of the band + new-cell list (every lane of the
-// warp calls it).
+// warp calls it).  kAppend: append the cells that stay or become interface
+// to the next interface list (the batched step); a single domain rebuilds
+// that list in cell order with k_compact_band instead.
+template <bool kAppend = true>
 __device__ __forceinline__ void finalize_warp(const DPtrs& d, const KParams& p, int parity,
                                               int base) {
   const int* __restrict__ band = d.band[parity];
@@ -1537,8 +1540,12 @@ __device__ __forceinline__ void finalize_warp(const DPtrs& d, const KParams& p, 
         remaining &= ~__ballot_sync(0xffffffffu, mine);
       }
     }
-    const int pos = warp_append(&d.counts[parity ^ 1], keep);
-    if (keep) next[pos] = c;
+    if constexpr (kAppend) {
+      const int pos = warp_append(&d.counts[parity ^ 1], keep);
+      if (keep) next[pos] = c;
+    } else {
+      (void)next;
+    }
     mark_tile(d, p, keep ? c : -1, d.tiles[parity ^ 1], &d.counts[3 + (parity ^ 1)]);
     mark_seg(d, to_liq ? c : -1);
   }
@@ -1551,7 +1558,7 @@ static __global__ void __launch_bounds__(kBlock) k_finalize(DPtrs d, KParams p, 
   }
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  for (int base = wid * 32; base < total; base += warps * 32) finalize_warp(d, p, parity, base);
+  for (int base = wid * 32; base < total; base += warps * 32) finalize_warp<false>(d, p, parity, base);
 }
 
 // p^V_b = p^V_b(0) V_b(0) / V_b (Eq. nm-fslbm-pressure-volume).

@@ -63,7 +63,7 @@ def test_batch_matches_members_alone_fp64(gpu_lib):
         a.step(5)
     for k, (a, m) in enumerate(zip(alone, members)):
         _assert_same(a, m, f"member {k} after interleaving")
-    assert batch.launches() == 45 * 10
+    assert batch.launches() == 45 * 11
     batch.close()
 
 
