@@ -8,6 +8,7 @@
 
 #include "fslbm_kernels.cuh"
 #include "fslbm_band_list.cuh"
+#include "fslbm_apply.cuh"
 
 namespace fslbm {
 
@@ -96,14 +97,23 @@ struct Engine {
       if (ev) ev->mark(4, st);
       k_count<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
       if (ev) ev->mark(5, st);
-      k_apply<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+      // the two independent parts of the apply stage, side by side in the
+      // graph (one after the other while stages are timed)
+      const bool side = fk && !ev;
+      if (side) {
+        cudaEventRecord(fk->fork, st);
+        cudaStreamWaitEvent(fk->side, fk->fork, 0);
+      }
+      k_apply_new<Q, S><<<band_grid, 128, 0, side ? fk->side : st>>>(d, p, parity);
+      if (side) cudaEventRecord(fk->join, fk->side);
+      k_apply_band<Q, S><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
+      if (side) cudaStreamWaitEvent(st, fk->join, 0);
       if (ev) ev->mark(6, st);
       k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
       k_compact_band<<<compact_grid(p, band_grid), kBlock, 0, st>>>(d, p, parity);
       if (ev) ev->mark(7, st);
       if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
       if (ev) ev->mark(8, st);
-      (void)fk;
       return;
     }
     auto bulk = [&](cudaStream_t s2) {
@@ -252,7 +262,7 @@ struct Engine {
       o.bulk_fn[7] = (const void*)&k_bulk<Q, S, 7>;
     }
     o.bulk_blocks_per_sm = bulk_blocks_per_sm();
-    o.step_launches = kFusedGeo ? 7 : 8;
+    o.step_launches = 8;  // fused: the apply stage is two kernels
     o.bulk_smem = kTmaBulk ? tma_smem<Q, typename S::T>() : kFusedGeo ? geometry_smem<typename S::Real>() : 0;
     o.batch_step = &batch_step;
     // two plan kernels, geometry, bulk sweep, interface update, resolve,

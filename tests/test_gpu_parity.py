@@ -200,8 +200,9 @@ def test_timing_mode_matches_graph_mode(gpu_lib):
     np.testing.assert_array_equal(ra["pdf"], rb["pdf"])
     times, launches = b.stage_times()
     assert launches == 20 * 8 and times["bulk"] > 0
-    # the FP32 engine folds the geometry pass into the bulk sweep: one launch
-    # less a step, the same results in both modes
+    # the FP32 engine folds the geometry pass into the bulk sweep and splits
+    # the apply stage in two kernels: as many launches, the same results in
+    # both modes
     a = fslbm.context_for(sc, precision="FP32")
     b = fslbm.context_for(sc, precision="FP32")
     b.set_timing(True)
@@ -210,7 +211,7 @@ def test_timing_mode_matches_graph_mode(gpu_lib):
     ra, rb = a.read(), b.read()
     np.testing.assert_array_equal(ra["pdf"], rb["pdf"])
     times, launches = b.stage_times()
-    assert launches == 20 * 7 and times["bulk"] > 0
+    assert launches == 20 * 8 and times["bulk"] > 0
 
 
 def test_reinit_matches_fresh_context(gpu_lib):
