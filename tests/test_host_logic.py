@@ -107,3 +107,41 @@ def test_compact_drop_expands_to_the_full_arrays():
                      (full.density, back.density)):
             np.testing.assert_array_equal(a, b)
         assert back.meta == full.meta and back.shape == full.shape
+
+
+def test_request_replay_and_expander():
+    """The serving benchmark's replay: requests start no earlier than their
+    arrival, every one finishes once, time-to-result is measured from the
+    arrival, and the worker-thread expansion gives the generator's arrays."""
+    import sys
+    import os
+    import time
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    trace = S.drop_requests(n=5, rate=50.0, lo=20, hi=28)
+    comp = [S.drop_impact_compact(**kw) for _, kw in trace]
+    arrivals = [t for t, _ in trace]
+    exp = bench._Expander(comp, 2)
+    started = {}
+    t0 = [None]
+
+    def step(ready):
+        if t0[0] is None:
+            t0[0] = time.perf_counter()
+        exp.prefetch(ready)
+        if not ready:
+            return [], False
+        k = ready.pop(0)
+        started[k] = time.perf_counter() - t0[0]
+        sc = exp.take(k)
+        full = S.drop_impact(**trace[k][1])
+        np.testing.assert_array_equal(sc.velocity, full.velocity)
+        return [(k, {"k": k})], True
+
+    res, makespan = bench._replay(arrivals, step)
+    exp.close()
+    assert sorted(res) == list(range(5))
+    for k in range(5):
+        assert started[k] >= arrivals[k] - 0.05
+        assert res[k]["ttr"] >= 0.0
+    assert makespan >= arrivals[-1] - 0.05
