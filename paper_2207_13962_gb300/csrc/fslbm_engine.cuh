@@ -93,7 +93,8 @@ struct Engine {
         k_interface<Q, S, decltype(C)::value><<<band_grid * 2, 128, 0, st>>>(d, p, parity);
       });
       if (ev) ev->mark(3, st);
-      k_resolve<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
+      // three resident blocks per SM (75 registers): about one band cell a thread
+      k_resolve<Q><<<band_grid * 3 / 2, kBlock, 0, st>>>(d, p, parity);
       if (ev) ev->mark(4, st);
       k_count<Q><<<band_grid, kBlock, 0, st>>>(d, p, parity);
       if (ev) ev->mark(5, st);
@@ -110,9 +111,20 @@ struct Engine {
       if (side) cudaStreamWaitEvent(st, fk->join, 0);
       if (ev) ev->mark(6, st);
       k_finalize<<<band_grid, kBlock, 0, st>>>(d, p, parity);
+      // the bubble pressures (from finalize's sums) and the list rebuild (from
+      // its flags) are independent: side by side in the graph as well
+      const bool bub = p.bubble_model && d.nb > 0;
+      const bool bub_side = side && bub;
+      if (bub_side) {
+        cudaEventRecord(fk->fork, st);
+        cudaStreamWaitEvent(fk->side, fk->fork, 0);
+        k_bubble<<<1, 256, 0, fk->side>>>(d, p);
+        cudaEventRecord(fk->join, fk->side);
+      }
       k_compact_band<<<compact_grid(p, band_grid), kBlock, 0, st>>>(d, p, parity);
       if (ev) ev->mark(7, st);
-      if (p.bubble_model && d.nb > 0) k_bubble<<<1, 256, 0, st>>>(d, p);
+      if (bub && !bub_side) k_bubble<<<1, 256, 0, st>>>(d, p);
+      if (bub_side) cudaStreamWaitEvent(st, fk->join, 0);
       if (ev) ev->mark(8, st);
       return;
     }
