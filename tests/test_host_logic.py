@@ -145,3 +145,19 @@ def test_request_replay_and_expander():
         assert started[k] >= arrivals[k] - 0.05
         assert res[k]["ttr"] >= 0.0
     assert makespan >= arrivals[-1] - 0.05
+
+
+def test_openmp_oracle_equals_single_thread():
+    """The all-core CPU baseline times the oracle built with OpenMP over its
+    stream-collide cell loop; it must compute exactly what the single-thread
+    oracle computes (each cell's arithmetic is independent of the others)."""
+    from oracle import Oracle
+    sc = S.random_interface(shape=(14, 12, 9), seed=5)
+    runs = []
+    for omp in (False, True):
+        o = Oracle(*sc.shape, **S.make_oracle_kwargs(sc), openmp=omp)
+        o.init(sc.fill, sc.flags, sc.velocity, sc.density)
+        o.step(12)
+        runs.append(o.read())
+    for key in ("pdf", "fill", "flags", "mass"):
+        np.testing.assert_array_equal(runs[0][key], runs[1][key], err_msg=key)
